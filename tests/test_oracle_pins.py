@@ -1,0 +1,384 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's formulas: each compares it with a closed
+form, a hand-derived worked example (tests/golden), an independent route
+(brute-force KKT enumeration, scipy minimisation, finite differences, LAPACK
+eigenvalues) or an exact algebraic relation the paper derives (identity_lag,
+S_k = theta_k^2, the averaged-iterate feasibility identity), chosen so that a
+dropped term, a wrong sign, a wrong step size or a shifted index fails one.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from oracle.kkt import solve_kkt
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ALGS = (O.DGM, O.DFGM, O.ADGM, O.ADFGM)
+
+
+def _qp(inst, cone=O.CONE_INEQ):
+    return O.QP(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, cone)
+
+
+def _golden(name):
+    with open(os.path.join(GOLD, name)) as f:
+        d = json.load(f)
+    qp = O.QP(np.array(d["Q"]), np.array(d["q"]), np.array(d["G"]), np.array(d["g"]),
+              np.array(d["lb"]), np.array(d["ub"]))
+    return qp, d
+
+
+def _small(seed, n=6, p=4, g_scale=0.02, box=1.0):
+    inst = W.single_dense(n=n, p=p, seed=seed, lam_lo=1.0, lam_hi=10.0, g_scale=g_scale, box=box)
+    return inst, _qp(inst)
+
+
+# --------------------------------------------------------------- worked examples
+
+@pytest.mark.parametrize("name", ["two_var_qp.json", "box_and_constraint_qp.json"])
+@pytest.mark.parametrize("alg", ALGS)
+def test_golden_worked_example(name, alg):
+    qp, d = _golden(name)
+    c = O.constants(qp, alg)
+    r = O.dfom(qp, alg, c, eps_in=1e-13, eps_out=1e-9, max_outer=200000, max_inner=100000)
+    assert r.status == 0
+    np.testing.assert_allclose(r.x_last, d["x_star"], atol=2e-5)
+    assert abs(r.f_last - d["F_star"]) < 1e-6
+    # the averaged output converges at O(1/k) (DGM) / O(1/k^2) (DFGM): looser target
+    ra = O.dfom(qp, alg, c, eps_in=1e-10, eps_out=1e-4, max_outer=400000, want_last=False)
+    assert ra.status == 0 and ra.converged_avg
+    np.testing.assert_allclose(ra.x_avg, d["x_star"], atol=1e-2)
+    assert abs(ra.f_avg - d["F_star"]) < 1e-3
+    if alg in (O.DGM, O.DFGM):  # rho = 0: the dual iterate is the Lagrange multiplier
+        np.testing.assert_allclose(r.lam, d["lambda_star"], atol=1e-3)
+
+
+def test_golden_kkt_enumeration_agrees():
+    for name in ("two_var_qp.json", "box_and_constraint_qp.json"):
+        qp, d = _golden(name)
+        x, lam, f = solve_kkt(qp.Q, qp.q, qp.G, qp.g, qp.lb, qp.ub)
+        np.testing.assert_allclose(x, d["x_star"], atol=1e-12)
+        np.testing.assert_allclose(lam, d["lambda_star"], atol=1e-12)
+        assert abs(f - d["F_star"]) < 1e-12
+
+
+# ------------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("variant", [O.INNER_GM, O.INNER_FGM, O.INNER_FGMSIGMA])
+def test_fom_box_only_diagonal_closed_form(variant):
+    """p = 0 (Sec. 3: FOM applied directly when X_QP is simple): diagonal Q gives clamp(-q/Q_ii)."""
+    rng = np.random.default_rng(5)
+    n = 12
+    d = rng.uniform(0.5, 5.0, n)
+    q = rng.standard_normal(n) * 4
+    qp = O.QP(np.diag(d), q, np.zeros((0, n)), np.zeros(0), -np.ones(n), np.ones(n))
+    x, k, _ = O.fom(qp, 0.0, np.zeros(1), d.max(), d.min(), np.zeros(n), variant=variant,
+                    fixed=3000)
+    np.testing.assert_allclose(x, np.clip(-q / d, -1, 1), atol=1e-12)
+
+
+def test_fom_unconstrained_interior():
+    """Interior minimiser: FOM converges to -Q^{-1} q when the box is inactive."""
+    inst = W.single_dense(n=20, p=0, seed=3, lam_lo=1.0, lam_hi=20.0, box=1e3)
+    qp = _qp(inst)
+    xs = -np.linalg.solve(inst.Q, inst.q)
+    x, _, _ = O.fom(qp, 0.0, np.zeros(1), inst.lmax_Q, inst.lmin_Q, np.zeros(20), fixed=2000)
+    np.testing.assert_allclose(x, xs, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_single_constraint_closed_form(alg):
+    """One constraint a'x + g <= 0, inactive box: lambda* = max(0, (g - a'Q^-1 q)/(a'Q^-1 a))."""
+    inst = W.single_dense(n=8, p=1, seed=11, lam_lo=1.0, lam_hi=5.0, box=1e3)
+    a = inst.G[0]
+    Qi_q = np.linalg.solve(inst.Q, inst.q)
+    Qi_a = np.linalg.solve(inst.Q, a)
+    g = float(a @ Qi_q + 0.5)  # makes the unconstrained minimiser violate the constraint
+    lam = max(0.0, (g - a @ Qi_q) / (a @ Qi_a))
+    xs = -(Qi_q + lam * Qi_a)
+    qp = O.QP(inst.Q, inst.q, a[None, :], np.array([g]), inst.lb, inst.ub)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    r = O.dfom(qp, alg, c, eps_in=1e-14, eps_out=1e-10, max_outer=200000)
+    np.testing.assert_allclose(r.x_last, xs, atol=1e-5)
+    if alg in (O.DGM, O.DFGM):
+        assert abs(r.lam[0] - lam) < 1e-4
+
+
+def test_inactive_constraints_keep_lambda_zero():
+    """lambda^0 = 0 and G ubar + g < 0 at every inner solution: the update of Algorithm DFOM keeps lambda = 0."""
+    inst = W.single_dense(seed=0)  # the n=50, p=25 FP64 case: constraints inactive
+    qp = _qp(inst)
+    for alg in (O.DGM, O.DFGM):
+        c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+        r = O.dfom(qp, alg, c, inner_fixed=200, outer_fixed=5)
+        assert np.all(r.lam == 0.0)
+
+
+# --------------------------------------------------------------- brute force KKT
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("alg", ALGS)
+def test_matches_kkt_enumeration_box_active(seed, alg):
+    inst, qp = _small(seed, n=5, p=4, g_scale=0.02, box=0.3)
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    r = O.dfom(qp, alg, c, eps_in=1e-12, eps_out=1e-8, max_outer=400000)
+    assert r.status == 0
+    np.testing.assert_allclose(r.x_last, xs, atol=1e-3)
+    assert abs(r.f_last - fs) <= 1e-7 + 1e-6 * abs(fs)
+    assert r.d_lb <= fs + 1e-10          # the certificate's lower bound never exceeds F*
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_matches_kkt_enumeration_wide_box(seed):
+    inst, qp = _small(seed, n=8, p=9, g_scale=0.02, box=50.0)
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, box_active=False)
+    for alg in ALGS:
+        c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+        r = O.dfom(qp, alg, c, eps_in=1e-12, eps_out=1e-8, max_outer=400000)
+        np.testing.assert_allclose(r.x_last, xs, atol=1e-4)
+
+
+def test_equality_cone_matches_kkt():
+    """K = {0} (equality constraints, Sec. 2): K_d = R^p."""
+    inst, _ = _small(7, n=6, p=2, box=50.0)
+    qp = O.QP(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, O.CONE_EQ)
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, box_active=False,
+                              equality=True)
+    for alg in (O.DFGM, O.ADFGM):
+        c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+        r = O.dfom(qp, alg, c, eps_in=1e-12, eps_out=1e-9, max_outer=400000)
+        np.testing.assert_allclose(r.x_last, xs, atol=1e-5)
+
+
+# --------------------------------------------- Lagrangian, gradients, definitions
+
+@pytest.mark.parametrize("rho", [0.0, 0.7])
+@pytest.mark.parametrize("cone", [O.CONE_INEQ, O.CONE_EQ])
+def test_lagrangian_is_min_over_s(rho, cone):
+    """eq. auglag1 equals the minimum over s in K of eq. auglag (scipy L-BFGS-B on s)."""
+    from scipy.optimize import minimize
+    inst, _ = _small(8, n=6, p=5, g_scale=1.0)
+    qp = O.QP(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, cone)
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        u = rng.uniform(-1, 1, 6)
+        lam = rng.standard_normal(5)
+        r = inst.G @ u + inst.g
+        Fu = 0.5 * u @ inst.Q @ u + inst.q @ u
+        if cone == O.CONE_EQ or rho == 0.0:
+            # K = {0} forces s = 0; rho = 0 with K = R^p_- is linear in s and the
+            # formula of eq. auglag1 takes s = 0 (the value at s(u, lambda))
+            ref = Fu + lam @ r + 0.5 * rho * r @ r
+        else:
+            obj = lambda s: lam @ (r - s) + 0.5 * rho * (r - s) @ (r - s)
+            jac = lambda s: -lam - rho * (r - s)
+            m = minimize(obj, np.minimum(r, 0), jac=jac, bounds=[(None, 0.0)] * 5, method="L-BFGS-B",
+                         options=dict(ftol=1e-15, gtol=1e-12))
+            ref = Fu + m.fun
+        assert abs(O.lagrangian(qp, rho, u, lam) - ref) < 1e-9
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.7])
+def test_grad_lagr_finite_differences(rho):
+    inst, qp = _small(9, n=7, p=5, g_scale=0.02)
+    rng = np.random.default_rng(1)
+    u = rng.uniform(-1, 1, 7)
+    lam = np.abs(rng.standard_normal(5))
+    gr = O.grad_lagr(qp, rho, u, lam)
+    h = 1e-6
+    fd = np.array([(O.lagrangian(qp, rho, u + h * e, lam) - O.lagrangian(qp, rho, u - h * e, lam)) / (2 * h)
+                   for e in np.eye(7)])
+    np.testing.assert_allclose(gr, fd, atol=1e-7)
+
+
+def _dual_value(qp, rho, lam, c):
+    x, _, _ = O.fom(qp, rho, lam, c.LL, c.sigma, np.zeros(qp.n), eps_in=1e-15, max_inner=20000)
+    return O.lagrangian(qp, rho, x, lam), x
+
+
+@pytest.mark.parametrize("alg", [O.DFGM, O.ADFGM])
+def test_dual_gradient_matches_finite_differences(alg):
+    """eq. Ld: grad d_rho(lambda) = G u(lambda) + g - s(u(lambda), lambda)."""
+    inst, qp = _small(10, n=6, p=4, g_scale=0.02, box=0.5)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    lam = np.array([0.3, 0.0, 0.8, 0.1])
+    _, x = _dual_value(qp, c.rho, lam, c)
+    grad = O.dual_grad(qp, c.rho, x, lam)
+    h = 1e-5
+    fd = np.array([(_dual_value(qp, c.rho, lam + h * e, c)[0] - _dual_value(qp, c.rho, lam - h * e, c)[0]) / (2 * h)
+                   for e in np.eye(4)])
+    np.testing.assert_allclose(grad, fd, atol=2e-6)
+
+
+@pytest.mark.parametrize("alg", [O.DFGM, O.ADFGM])
+def test_dual_lipschitz_constant(alg):
+    """L_d of eq. Ld bounds ||grad d(l1) - grad d(l2)|| / ||l1 - l2||."""
+    inst, qp = _small(12, n=6, p=4, g_scale=0.02, box=0.5)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    rng = np.random.default_rng(2)
+    for _ in range(5):
+        l1, l2 = np.abs(rng.standard_normal(4)) * 3, np.abs(rng.standard_normal(4)) * 3
+        _, x1 = _dual_value(qp, c.rho, l1, c)
+        _, x2 = _dual_value(qp, c.rho, l2, c)
+        g1, g2 = O.dual_grad(qp, c.rho, x1, l1), O.dual_grad(qp, c.rho, x2, l2)
+        assert np.linalg.norm(g1 - g2) <= c.Ld * np.linalg.norm(l1 - l2) * (1 + 1e-9)
+
+
+def test_power_iteration_matches_lapack():
+    inst = W.single_dense(n=40, p=20, seed=13)
+    qp = _qp(inst)
+    assert abs(O.power_lmax(qp, "Q", 3000) - np.linalg.eigvalsh(inst.Q)[-1]) < 1e-8 * inst.lmax_Q
+    assert abs(O.power_lmax(qp, "GtG", 3000) - np.linalg.norm(inst.G, 2) ** 2) < 1e-8
+
+
+# ------------------------------------------------------ invariants of the paper
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_identity_lag_every_outer(alg):
+    """eq. identity_lag: dbar(mu) - <grad dbar(mu), mu> = F(ubar) + rho/2 ||grad dbar(mu)||^2."""
+    inst, qp = _small(14, n=10, p=8, g_scale=0.02)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    r = O.dfom(qp, alg, c, eps_in=1e-8, outer_fixed=40, trace_cap=40)
+    t = r.trace
+    lhs = t[:, 5] - t[:, 6]
+    rhs = t[:, 7] + 0.5 * c.rho * t[:, 8]
+    np.testing.assert_allclose(lhs, rhs, atol=1e-11)
+    assert np.all(t[:, 9] >= 0.0)  # lambda^k in K_d = R^p_+
+
+
+@pytest.mark.parametrize("alg", [O.DFGM, O.ADFGM])
+def test_theta_sequence(alg):
+    """eq. fg_step: (k+1)/2 <= theta_k <= k and S_k = sum theta_j = theta_k^2."""
+    inst, qp = _small(15)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    r = O.dfom(qp, alg, c, inner_fixed=5, outer_fixed=60, trace_cap=60)
+    k, th, S = r.trace[:, 0], r.trace[:, 1], r.trace[:, 2]
+    assert np.all((k + 1) / 2 <= th + 1e-12) and np.all(th <= k + 1e-12)
+    np.testing.assert_allclose(S, th ** 2, rtol=1e-12)
+    # momentum weight beta_k = (theta_k - 1)/theta_{k+1}
+    np.testing.assert_allclose(r.trace[:-1, 3], (th[:-1] - 1) / th[1:], rtol=1e-12)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_box_and_dual_cone_invariants(alg):
+    inst, qp = _small(16, n=12, p=10, g_scale=0.02, box=0.4)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    r = O.dfom(qp, alg, c, eps_in=1e-7, outer_fixed=30)
+    assert np.all(r.x_last >= -0.4) and np.all(r.x_last <= 0.4)
+    assert np.all(r.x_avg >= -0.4 - 1e-15) and np.all(r.x_avg <= 0.4 + 1e-15)
+    assert np.all(r.lam >= 0.0)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+@pytest.mark.parametrize("K", [1, 2, 7, 25])
+def test_average_feasibility_identity(alg, K):
+    """Averaged-iterate feasibility (Sec. 4.2, proofs of eq. feasibility_final and eq. infes_av):
+    with l^k = lambda^{k-1} + theta_k (lambda^k - lambda^{k-1}), summing the dual steps gives
+    dist_K(G uhat^k + g) <= (2 L_d / S_k) ||l^k - lambda^0||  exactly (inexact inner solves
+    included).  The paper prints the factor L_d / S_k; the summation it describes gives 2 L_d / S_k.
+    DGM is the case theta = 1, S_k = k, l^k = lambda^k."""
+    inst, qp = _small(17, n=10, p=8, g_scale=0.02)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    kw = dict(eps_in=1e-4, want_last=False)
+    rK = O.dfom(qp, alg, c, outer_fixed=K, trace_cap=K, **kw)
+    lam_prev = O.dfom(qp, alg, c, outer_fixed=K - 1, **kw).lam if K > 1 else np.zeros(qp.p)
+    theta_K, S_K = rK.trace[-1, 1], rK.trace[-1, 2]
+    l_K = lam_prev + theta_K * (rK.lam - lam_prev)
+    bound = 2 * c.Ld / S_K * np.linalg.norm(l_K)
+    assert O.infeas(qp, rK.x_avg) <= bound * (1 + 1e-10) + 1e-14
+
+
+# ---------------------------------------------------------- rate bounds of the paper
+
+@pytest.mark.parametrize("variant,power", [(O.INNER_GM, 1), (O.INNER_FGM, 2)])
+def test_fom_rate_lemma(variant, power):
+    """eq. bound_gen_dfg1 with sigma = 0: phi(x^k) - phi* <= 2 L R^2 / (k+1)^{p(beta)}."""
+    inst, qp = _small(18, n=10, p=6, g_scale=0.02, box=0.5)
+    mu = np.full(6, 0.5)
+    LL = inst.lmax_Q
+    xstar, _, _ = O.fom(qp, 0.0, mu, LL, inst.lmin_Q, np.zeros(10), fixed=20000)
+    phistar = O.lagrangian(qp, 0.0, xstar, mu)
+    R2 = float(np.sum(xstar ** 2))
+    _, _, phi = O.fom(qp, 0.0, mu, LL, 0.0, np.zeros(10), variant=variant, fixed=300, phi_trace=300)
+    k = np.arange(1, 301)
+    assert np.all(phi - phistar <= 2 * LL * R2 / (k + 1.0) ** power + 1e-12)
+
+
+def test_fom_rate_lemma_strongly_convex():
+    """eq. bound_gen_dfg1 with sigma > 0 (FGM_sigma): (1 - sqrt(sigma/L))^{k-1} L R^2."""
+    inst, qp = _small(19, n=10, p=6, g_scale=0.02, box=0.5)
+    mu = np.full(6, 0.5)
+    L, s = inst.lmax_Q, inst.lmin_Q
+    xstar, _, _ = O.fom(qp, 0.0, mu, L, s, np.zeros(10), fixed=20000)
+    phistar = O.lagrangian(qp, 0.0, xstar, mu)
+    R2 = float(np.sum(xstar ** 2))
+    _, _, phi = O.fom(qp, 0.0, mu, L, s, np.zeros(10), variant=O.INNER_FGMSIGMA, fixed=200,
+                      phi_trace=200)
+    k = np.arange(1, 201)
+    bound = np.minimum((1 - math.sqrt(s / L)) ** (k - 1) * L * R2, 2 * L * R2 / (k + 1.0) ** 2)
+    assert np.all(phi - phistar <= bound + 1e-12)
+
+
+@pytest.mark.parametrize("alg,power", [(O.DGM, 1), (O.DFGM, 2), (O.ADGM, 1), (O.ADFGM, 2)])
+def test_dual_rate_theorem(alg, power):
+    """eq. bound_gen_dfg: F* - d_rho(lambda^k) <= 4 L_d R_d^2/(k+1)^p + 2 (k+1)^{p-1} eps_in."""
+    inst, qp = _small(20, n=5, p=4, g_scale=0.02, box=0.3)
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    # R_d = dist(lambda^0 = 0, Lambda*); Lambda* of the augmented dual contains lambda*
+    Rd = float(np.linalg.norm(lam_s))
+    eps_in = 1e-6
+    for k in (1, 3, 10, 30):
+        r = O.dfom(qp, alg, c, eps_in=eps_in, outer_fixed=k, want_last=False)
+        d_k, _ = _dual_value(qp, c.rho, r.lam, c)
+        assert fs - d_k <= 4 * c.Ld * Rd ** 2 / (k + 1) ** power + 2 * (k + 1) ** (power - 1) * eps_in + 1e-12
+
+
+def test_dgm_dual_sequence_bound():
+    """eq. bound_seq_dgm: ||lambda^k - lambda*|| <= R_d + sqrt(k eps_in / L_d) (DGM)."""
+    inst, qp = _small(21, n=5, p=4, g_scale=0.02, box=0.3)
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+    c = O.constants(qp, O.DGM, lmin_Q=inst.lmin_Q)
+    Rd = float(np.linalg.norm(lam_s))
+    eps_in = 1e-5
+    for k in (1, 5, 20, 80):
+        r = O.dfom(qp, O.DGM, c, eps_in=eps_in, outer_fixed=k, want_last=False)
+        assert np.linalg.norm(r.lam - lam_s) <= Rd + math.sqrt(k * eps_in / c.Ld) + 1e-12
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_certificate_implies_eps_optimality(alg):
+    """A converged run (certificate mode) is eps-primal optimal against brute-force F*."""
+    inst, qp = _small(22, n=5, p=4, g_scale=0.02, box=0.3)
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    eps = 1e-3
+    r = O.dfom(qp, alg, c, eps_in=O.default_eps_in(alg, eps, c.Ld), eps_out=eps, max_outer=100000)
+    assert r.status == 0
+    assert r.d_lb <= fs + 1e-12
+    if r.converged_last:
+        assert r.infeas_last <= eps and r.f_last - fs <= eps
+        assert fs - r.f_last <= np.linalg.norm(lam_s) * r.infeas_last + 1e-12
+    if r.converged_avg:
+        assert r.infeas_avg <= eps and r.f_avg - fs <= eps
+
+
+def test_inner_fixed_count_bound_strongly_convex():
+    """Sec. 5: k_in = sqrt(L/sigma) log(L D_U^2 / eps_in) + 1 iterations of FGM_sigma give an eps_in-solution."""
+    inst, qp = _small(23, n=10, p=6, g_scale=0.02, box=0.5)
+    mu = np.full(6, 0.3)
+    L, s = inst.lmax_Q, inst.lmin_Q
+    D2 = float(np.sum((inst.ub - inst.lb) ** 2))
+    xstar, _, _ = O.fom(qp, 0.0, mu, L, s, np.zeros(10), fixed=20000)
+    phistar = O.lagrangian(qp, 0.0, xstar, mu)
+    for eps_in in (1e-3, 1e-6):
+        kin = int(math.ceil(math.sqrt(L / s) * math.log(L * D2 / eps_in) + 1))
+        x, _, _ = O.fom(qp, 0.0, mu, L, s, np.zeros(10), fixed=kin)
+        assert O.lagrangian(qp, 0.0, x, mu) - phistar <= eps_in

@@ -1,0 +1,194 @@
+"""Seeded synthetic QP generators shared by the tests, the benchmark and the oracle.
+
+This module only draws random data; it holds none of the solver's arithmetic.
+The instances stand in for the paper's random QPs (Sec. 6 of arXiv 1504.05708
+uses randomly generated QPs and no public dataset):
+
+  single_dense      dense QP with Q = U diag(Lambda) U', U Haar-orthogonal,
+                    Lambda ~ U[lmin, lmax]; q ~ N(0,1); G ~ N(0, 1/n);
+                    g = -|N(0,1)| - 0.1 (x = 0 strictly feasible); box [-1, 1].
+                    n=50, p=25, Lambda ~ U[1,100], seed 0 is the FP64 case.
+  large_dense       Q = M'M/n + 0.01 I with M ~ N(0,1) n x n; q ~ N(0,1);
+                    G ~ N(0,1/n); g = -|N(0,1)| - 0.1; box [-1,1];
+                    n=20000, p=10000 is the large FP32 case.
+  mpc_batch         condensed MPC: nx=12, nu=4, horizon N=25 (n=100, p=600),
+                    A random with spectral radius 0.95, B ~ N(0,1), Qx=I, R=0.1I,
+                    B instances differing only in x0 ~ N(0,I).
+  uneven_batch      instances as single_dense with n ~ U{16..512}, p = n/2,
+                    kappa(Q) ~ U[10, 1e4] (lambda_1 = 1, lambda_n = kappa),
+                    algorithm uniform over DGM/DFGM/ADGM/ADFGM.
+  served_stream     Poisson arrival times and request mix for the served case.
+
+Every generator returns known eigenvalue bounds (lmin_Q) where the
+construction fixes them, so both the oracle and the GPU path can be handed
+the same constants.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+ALGS = ("DGM", "DFGM", "ADGM", "ADFGM")
+
+
+@dataclass
+class Instance:
+    Q: np.ndarray
+    q: np.ndarray
+    G: np.ndarray
+    g: np.ndarray
+    lb: np.ndarray
+    ub: np.ndarray
+    lmin_Q: float
+    lmax_Q: float | None = None
+    alg: str = "DFGM"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self):
+        return self.q.shape[0]
+
+    @property
+    def p(self):
+        return self.g.shape[0]
+
+
+def haar(rng: np.random.Generator, n: int) -> np.ndarray:
+    """Haar-distributed orthogonal matrix: QR of a Gaussian with sign correction."""
+    Z = rng.standard_normal((n, n))
+    Qm, R = np.linalg.qr(Z)
+    return Qm * np.sign(np.diag(R))[None, :]
+
+
+def single_dense(n=50, p=25, seed=0, lam_lo=1.0, lam_hi=100.0, g_scale=1.0, g_offset=0.1,
+                 box=1.0, alg="DFGM", kappa=None) -> Instance:
+    """Dense QP with a prescribed spectrum (see module docstring).
+
+    kappa given: lambda_1 = 1, lambda_n = kappa, the rest U[1, kappa].
+    g_scale < 1 makes constraints active more often (parity variants)."""
+    rng = np.random.default_rng(seed)
+    U = haar(rng, n)
+    if kappa is None:
+        lam = rng.uniform(lam_lo, lam_hi, n)
+    else:
+        lam = np.concatenate([[1.0, kappa], rng.uniform(1.0, kappa, max(n - 2, 0))])[:n]
+    Q = (U * lam[None, :]) @ U.T
+    Q = 0.5 * (Q + Q.T)
+    q = rng.standard_normal(n)
+    G = rng.standard_normal((p, n)) / np.sqrt(n)
+    g = -np.abs(rng.standard_normal(p)) * g_scale - g_offset
+    lb = -box * np.ones(n)
+    ub = box * np.ones(n)
+    return Instance(Q, q, G, g, lb, ub, float(lam.min()), float(lam.max()), alg,
+                    {"kind": "single_dense", "seed": seed})
+
+
+def large_dense(n=20000, p=10000, seed=1, device="cpu", dtype=None):
+    """Large dense QP, Q = M'M/n + 0.01 I (lambda_min(Q) >= 0.01 by construction).
+
+    Built with torch so the full-size case can be drawn directly in device
+    memory; returns a dict of torch tensors (Q, q, G, g, lb, ub) plus lmin_Q."""
+    import torch
+
+    dtype = dtype or torch.float32
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    work = torch.float64 if (device == "cpu" or n <= 4096) else torch.float32
+    M = torch.randn(n, n, generator=gen, device=device, dtype=work)
+    Q = (M.T @ M) / n
+    del M
+    Q.diagonal().add_(0.01)
+    Q = 0.5 * (Q + Q.T)
+    q = torch.randn(n, generator=gen, device=device, dtype=work)
+    G = torch.randn(p, n, generator=gen, device=device, dtype=work) / (n ** 0.5)
+    g = -torch.randn(p, generator=gen, device=device, dtype=work).abs() - 0.1
+    lb = -torch.ones(n, device=device, dtype=work)
+    ub = torch.ones(n, device=device, dtype=work)
+    out = {k: v.to(dtype).contiguous() for k, v in dict(Q=Q, q=q, G=G, g=g, lb=lb, ub=ub).items()}
+    out["lmin_Q"] = 0.01
+    return out
+
+
+def mpc_matrices(nx=12, nu=4, N=25, seed=2, rho_A=0.95):
+    """System matrices and condensing operators of the MPC case.
+
+    Returns dict with A, B, Gamma (N*nx x N*nu), Phi (N*nx x nx), Qbar, Rbar."""
+    rng = np.random.default_rng(seed)
+    A0 = rng.standard_normal((nx, nx))
+    A = rho_A * A0 / np.max(np.abs(np.linalg.eigvals(A0)))
+    B = rng.standard_normal((nx, nu))
+    Gamma = np.zeros((N * nx, N * nu))
+    Phi = np.zeros((N * nx, nx))
+    Ak = np.eye(nx)
+    powers = [np.eye(nx)]
+    for _ in range(N):
+        Ak = A @ Ak
+        powers.append(Ak)
+    for k in range(1, N + 1):  # state x_k, k = 1..N
+        Phi[(k - 1) * nx:k * nx] = powers[k]
+        for j in range(k):     # input u_j, j = 0..k-1
+            Gamma[(k - 1) * nx:k * nx, j * nu:(j + 1) * nu] = powers[k - 1 - j] @ B
+    return dict(A=A, B=B, Gamma=Gamma, Phi=Phi, Qbar=np.eye(N * nx), Rbar=0.1 * np.eye(N * nu),
+                nx=nx, nu=nu, N=N)
+
+
+def mpc_batch(batch=16384, nx=12, nu=4, N=25, seed=2, x0_seed=None):
+    """Condensed-MPC QPs sharing Q and G; q and g are affine in x0 ~ N(0, I).
+
+    Q = Gamma' Qbar Gamma + Rbar, q = Gamma' Qbar (Phi x0 - x_ref),
+    G = [Gamma; -Gamma], g = [Phi x0 - b; -Phi x0 - b], box |u| <= 1,
+    b = 1.05 max over the batch of max_k ||A^k x0||_inf (u = 0 strictly feasible),
+    x_ref = 1.2 b on state 1 and 0 elsewhere (so state bounds become active).
+    Returns dict(Q (n,n), G (p,n), qs (B,n), gs (B,p), lb, ub, lmin_Q, x0s)."""
+    m = mpc_matrices(nx, nu, N, seed)
+    rng = np.random.default_rng(seed + 1000 if x0_seed is None else x0_seed)
+    x0s = rng.standard_normal((batch, nx))
+    Gam, Phi = m["Gamma"], m["Phi"]
+    free = x0s @ Phi.T                      # (B, N*nx) free response
+    b = 1.05 * np.abs(free).max()
+    x_ref = np.zeros(N * nx)
+    x_ref[0::nx] = 1.2 * b
+    Q = Gam.T @ m["Qbar"] @ Gam + m["Rbar"]
+    Q = 0.5 * (Q + Q.T)
+    qs = (free - x_ref[None, :]) @ m["Qbar"] @ Gam
+    G = np.vstack([Gam, -Gam])
+    gs = np.hstack([free - b, -free - b])
+    n = N * nu
+    return dict(Q=Q, G=G, qs=qs, gs=gs, lb=-np.ones(n), ub=np.ones(n), lmin_Q=0.1, x0s=x0s, b=b)
+
+
+def uneven_sizes(count=10000, seed=3, n_lo=16, n_hi=512):
+    """Sizes, conditioning and algorithm of each uneven-batch instance."""
+    rng = np.random.default_rng(seed)
+    ns = rng.integers(n_lo, n_hi + 1, count)
+    kappas = rng.uniform(10.0, 1e4, count)
+    algs = rng.integers(0, 4, count)
+    seeds = rng.integers(0, 2**31 - 1, count)
+    return ns, kappas, algs, seeds
+
+
+def uneven_instance(n, kappa, alg, seed) -> Instance:
+    """One uneven-batch instance: as single_dense with p = n/2 and kappa(Q) = kappa."""
+    inst = single_dense(n=int(n), p=int(n) // 2, seed=int(seed), kappa=float(kappa),
+                        alg=ALGS[int(alg)])
+    inst.meta.update(kind="uneven", kappa=float(kappa))
+    return inst
+
+
+def uneven_batch(count=10000, seed=3, n_lo=16, n_hi=512):
+    """List of uneven-batch instances (CPU, FP64).  count=10000 is the full case."""
+    ns, kappas, algs, seeds = uneven_sizes(count, seed, n_lo, n_hi)
+    return [uneven_instance(n, k, a, s) for n, k, a, s in zip(ns, kappas, algs, seeds)]
+
+
+def served_stream(rate=20000.0, duration=60.0, seed=4, mpc_fraction=0.05):
+    """Poisson arrival times (s) and request kinds (0 = uneven-batch QP, 1 = MPC)."""
+    rng = np.random.default_rng(seed)
+    count = rng.poisson(rate * duration)
+    gaps = rng.exponential(1.0 / rate, count)
+    t = np.cumsum(gaps)
+    t = t[t < duration]
+    kinds = (rng.random(t.size) < mpc_fraction).astype(np.int32)
+    picks = rng.integers(0, 2**31 - 1, t.size)
+    return t, kinds, picks
