@@ -1,0 +1,205 @@
+/*
+ * duquad.h -- C ABI of the GB300 (sm_103a) DuQuad solver.
+ *
+ * Solves convex QPs of the form (Necoara & Patrascu, arXiv 1504.05708,
+ * Sec. 2, eq. original_primal):
+ *
+ *     min_{u in [lb, ub]}  F(u) = 1/2 u'Qu + q'u     s.t.  Gu + g in K,
+ *
+ * with K = R^p_- (inequalities, DQ_CONE_INEQ) or K = {0} (equalities,
+ * DQ_CONE_EQ), by the inexact (augmented) dual first-order method DFOM
+ * (Sec. 3): an outer projected dual (fast) gradient loop -- DGM / DFGM with
+ * rho = 0 (Case 1), ADGM / ADFGM with rho > 0 (Case 2) -- around an inner
+ * projected (fast) gradient solve of the (augmented) Lagrangian over the box
+ * (Algorithm FOM, Sec. 2.1), returning the last primal iterate (eq.
+ * last_primal) and/or the averaged primal iterate (eq. average_primal).
+ *
+ * Conventions for every entry point:
+ *   - Return value is a dq_status; nothing throws or aborts across the ABI.
+ *     A negative status means nothing was written to the caller's outputs;
+ *     dq_last_error() then returns a message for the calling thread.
+ *   - Matrices are dense row-major: Q is n x n (symmetric), G is p x n.
+ *   - Host arrays are always double.  Device arrays have the element type of
+ *     the problem's precision (double for DQ_FP64, float for DQ_FP32 and
+ *     DQ_BF16X3) and must stay valid while a handle borrows them.
+ *   - The caller owns every buffer it passes.  The library owns the handles
+ *     and the device memory it allocates for them (released by *_destroy).
+ *   - All GPU work is issued on the context's CUDA stream.  Entry points that
+ *     return host results synchronise that stream before returning.
+ */
+#ifndef DUQUAD_H
+#define DUQUAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Algorithm of the outer loop (Sec. 3, Algorithm DFOM and its DGM/DFGM rules).
+ * DQ_ADGM / DQ_ADFGM use the augmented Lagrangian (rho > 0, Case 2). */
+typedef enum { DQ_DGM = 0, DQ_DFGM = 1, DQ_ADGM = 2, DQ_ADFGM = 3 } dq_algorithm;
+
+/* Which primal output(s) to compute and test (eq. last_primal, eq. average_primal). */
+typedef enum { DQ_OUT_LAST = 1, DQ_OUT_AVERAGE = 2, DQ_OUT_BOTH = 3 } dq_output;
+
+/* Arithmetic of the solve.  DQ_FP64: everything in double.  DQ_FP32: iterates
+ * and matrix products in float, constants and final residuals in double.
+ * DQ_BF16X3: shared-matrix batches only; matrix products on tensor cores with
+ * bf16 hi/lo split operands (three products) and float accumulation. */
+typedef enum { DQ_FP64 = 0, DQ_FP32 = 1, DQ_BF16X3 = 2 } dq_precision;
+
+/* Inner stopping rule: DQ_INNER_GAP stops the inner loop of Algorithm FOM when
+ * the Frank-Wolfe gap of L_rho(., mu) over the box is <= eps_in (a certificate
+ * of eq. duquad_in); DQ_INNER_FIXED runs exactly fixed_inner iterations. */
+typedef enum { DQ_INNER_GAP = 0, DQ_INNER_FIXED = 1 } dq_inner_stop;
+
+typedef enum { DQ_CONE_INEQ = 0, DQ_CONE_EQ = 1 } dq_cone;
+typedef enum { DQ_HOST = 0, DQ_DEVICE = 1 } dq_memory;
+
+/* Engine selection (DQ_ENGINE_AUTO picks by size and batch). */
+typedef enum {
+  DQ_ENGINE_AUTO = 0,
+  DQ_ENGINE_CTA = 1,   /* whole solve inside one thread block per instance   */
+  DQ_ENGINE_GRID = 2,  /* one large instance spread over the whole GPU        */
+  DQ_ENGINE_TC = 3     /* shared-matrix batch on tensor cores (DQ_BF16X3)     */
+} dq_engine;
+
+typedef enum {
+  DQ_OK = 0,             /* converged (or fixed counts completed)             */
+  DQ_NOT_CONVERGED = 1,  /* max_outer reached; outputs hold the last iterates */
+  DQ_PENDING = 2,        /* dq_poll: the ticket is still running              */
+  DQ_ERR_INVALID = -1,   /* bad argument; message in dq_last_error()          */
+  DQ_ERR_NOMEM = -2,     /* device allocation failed                          */
+  DQ_ERR_CUDA = -3,      /* CUDA runtime error                                */
+  DQ_ERR_NONFINITE = -4, /* NaN/Inf appeared in the iterates                  */
+  DQ_ERR_DIVERGED = -5,  /* ||lambda|| grew past the divergence bound         */
+  DQ_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up                */
+  DQ_ERR_REJECTED = -7   /* serving: admission refused (footprint / queue)    */
+} dq_status;
+
+typedef struct dq_context dq_context;
+typedef struct dq_problem dq_problem;
+
+/* Problem description (eq. original_primal).  batch > 1 describes `batch`
+ * instances that share Q and G and differ in q (batch x n) and g (batch x p),
+ * all row-major.  lmax_Q, lmin_Q, normG2: NaN means "compute"; lmax_Q and
+ * normG2 are then found by FP64 power iteration on the GPU (Rayleigh quotient
+ * plus residual norm, so an upper estimate), lmin_Q is taken as 0 (valid for
+ * rho > 0 only).  A given value is used verbatim; lmin_Q must be a lower bound
+ * of lambda_min(Q) (it sets sigma_L and L_d of eq. Ld). */
+typedef struct {
+  int32_t n, p;            /* variables, linear constraints (p >= 0)           */
+  int32_t batch;           /* >= 1                                             */
+  int32_t cone;            /* dq_cone                                          */
+  int32_t prec;            /* dq_precision                                     */
+  int32_t memory;          /* dq_memory of the arrays below                    */
+  const void *Q, *q, *G, *g, *lb, *ub;
+  double lmax_Q, lmin_Q, normG2;
+} dq_problem_desc;
+
+/* Solve options.  NaN / 0 fields take the documented defaults. */
+typedef struct {
+  int32_t alg;             /* dq_algorithm                                     */
+  int32_t output;          /* dq_output (default DQ_OUT_BOTH)                  */
+  int32_t inner_stop;      /* dq_inner_stop                                    */
+  int32_t engine;          /* dq_engine                                        */
+  double eps_out;          /* outer certificate tolerance (default 1e-3)       */
+  double eps_in;           /* inner FW-gap tolerance (default: eq. choose_ein,
+                              eps_out/4 for (A)DGM, eps_out^1.5/(8 sqrt(2 L_d))
+                              for (A)DFGM with R_d = 1)                       */
+  double rho;              /* NaN: 0 for DGM/DFGM, 1/||G||^2 for ADGM/ADFGM    */
+  int32_t fixed_outer;     /* > 0: run exactly this many outer iterations      */
+  int32_t fixed_inner;     /* inner iterations for DQ_INNER_FIXED              */
+  int32_t max_outer;       /* cap in certificate mode (default 10000)          */
+  int32_t max_inner;       /* cap per inner solve in gap mode (default 5000)   */
+  int32_t check_every;     /* outer iterations between certificate checks (1)  */
+  int32_t inner_check_every; /* inner iterations between gap checks (1)        */
+  int32_t warm_start;      /* 1: start from the handle's last x and lambda     */
+  int32_t kd_literal;      /* 1: K_d = R^p when lmin_Q == 0 (paper's literal)  */
+  double Ld, LL, sigma;    /* NaN: derive from the problem's constants         */
+} dq_solve_opts;
+
+/* Result of one solve (one instance). */
+typedef struct {
+  int32_t status;          /* dq_status of this instance                       */
+  int32_t outer_iters;
+  int64_t inner_iters;     /* all inner iterations, extra last-iterate solves included */
+  int32_t converged_last, converged_avg;
+  double f_last, infeas_last;  /* FP64 F(u) and dist_K(Gu+g) of the outputs  */
+  double f_avg, infeas_avg;
+  double d_lb;             /* FP64 lower bound on F* from the certificate      */
+  double Ld, LL, sigma, rho, alpha; /* constants used (alpha = 1/(2 L_d))       */
+} dq_result;
+
+/* Output buffers.  NULL pointers are skipped.  memory = DQ_HOST: double
+ * arrays; DQ_DEVICE: device arrays of the precision's element type.  For a
+ * batch, arrays hold batch x n (x_last, x_avg) or batch x p (lambda) values. */
+typedef struct {
+  void *x_last, *x_avg, *lambda;
+  int32_t memory;
+} dq_outputs;
+
+/* Create a context bound to CUDA device `device` issuing work on the CUDA
+ * stream `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Errors: DQ_ERR_INVALID (bad device), DQ_ERR_CUDA. */
+dq_status dq_context_create(int device, void *cuda_stream, dq_context **out);
+dq_status dq_context_destroy(dq_context *ctx);
+
+/* Create a problem handle.  memory = DQ_HOST: the arrays are copied to the
+ * device (converted to the precision's element type).  memory = DQ_DEVICE:
+ * Q and G are borrowed (the caller keeps them alive and unchanged until
+ * dq_problem_destroy); vectors are copied.  The library also keeps a
+ * transposed copy of G and FP64 constants.  Validation: n >= 1, p >= 0,
+ * batch >= 1, lb <= ub (host data), finite values (host data);
+ * otherwise DQ_ERR_INVALID.  Errors: DQ_ERR_NOMEM, DQ_ERR_CUDA. */
+dq_status dq_problem_create(dq_context *ctx, const dq_problem_desc *desc, dq_problem **out);
+
+/* Replace q and/or g (NULL keeps the current one) of all `batch` instances;
+ * arrays as in dq_problem_desc with the given memory kind. */
+dq_status dq_problem_set_vectors(dq_problem *prob, const void *q, const void *g, int32_t memory);
+
+/* FP64 constants held by the handle (lambda_max(Q), lambda_min bound, ||G||^2). */
+dq_status dq_problem_constants(dq_problem *prob, double *lmax_Q, double *lmin_Q, double *normG2);
+
+dq_status dq_problem_destroy(dq_problem *prob);
+
+/* Solve the problem (all instances of a batch) with Algorithm DFOM (Sec. 3).
+ * results: one dq_result per instance (batch entries).  Outputs are written
+ * for status >= 0.  Returns the worst instance status (error < not converged
+ * < ok).  Synchronises the context's stream. */
+dq_status dq_solve(dq_problem *prob, const dq_solve_opts *opts, const dq_outputs *out,
+                   dq_result *results);
+
+/* Solve `count` independent problems of any sizes in one persistent launch
+ * (one CTA-resident solve per instance, a device work queue, longest
+ * instances first).  opts, out, results are arrays of `count` entries. */
+dq_status dq_solve_many(dq_problem *const *probs, int32_t count, const dq_solve_opts *opts,
+                        const dq_outputs *out, dq_result *results);
+
+/* ---- serving (continuous batching) ----------------------------------------
+ * dq_serve_start launches the context's persistent request loop with `slots`
+ * device request slots and a device-memory budget of `hbm_budget_bytes` for
+ * admitted requests.  dq_submit enqueues a solve of `prob` (which must stay
+ * alive until the ticket is polled) with new q/g vectors (host double, NULL
+ * keeps the handle's) and warm start from the handle's last lambda; it
+ * returns DQ_ERR_REJECTED when the request can never fit the budget.
+ * dq_poll returns DQ_PENDING until the ticket completes, then the result and
+ * the outputs (host double).  dq_serve_stop drains and stops the loop. */
+dq_status dq_serve_start(dq_context *ctx, int32_t slots, int64_t hbm_budget_bytes);
+dq_status dq_submit(dq_context *ctx, dq_problem *prob, const dq_solve_opts *opts,
+                    const double *q, const double *g, uint64_t *ticket);
+dq_status dq_poll(dq_context *ctx, uint64_t ticket, double *x_last, double *x_avg,
+                  double *lambda, dq_result *result);
+dq_status dq_serve_stop(dq_context *ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *dq_last_error(void);
+
+/* Library version string. */
+const char *dq_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DUQUAD_H */

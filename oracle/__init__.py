@@ -96,6 +96,8 @@ def _load():
             lib.orc_grad_lagr.argtypes = [qpp, d, dp, dp, dp]
             lib.orc_fw_gap.restype = d
             lib.orc_fw_gap.argtypes = [qpp, d, dp, dp]
+            lib.orc_inner_cert.restype = d
+            lib.orc_inner_cert.argtypes = [qpp, d, dp, dp, d, d]
             lib.orc_fom.restype = ctypes.c_int
             lib.orc_fom.argtypes = [qpp, d, dp, d, d, ctypes.c_int, ctypes.c_int, d, ctypes.c_int,
                                     ctypes.c_int, dp, dp, ctypes.c_int]
@@ -183,6 +185,12 @@ def grad_lagr(qp: QP, rho: float, u, lam) -> np.ndarray:
 def fw_gap(qp: QP, rho: float, x, lam) -> float:
     lam = _f64(lam) if qp.p else np.zeros(1)
     return _load().orc_fw_gap(ctypes.byref(qp._c()), rho, _dp(_f64(x)), _dp(lam))
+
+
+def inner_cert(qp: QP, rho: float, x, lam, LL: float, sigma: float) -> float:
+    """Upper bound on L_rho(x, lam) - d_rho(lam) used by the inner stopping rule (eq. duquad_in)."""
+    lam = _f64(lam) if qp.p else np.zeros(1)
+    return _load().orc_inner_cert(ctypes.byref(qp._c()), rho, _dp(_f64(x)), _dp(lam), LL, sigma)
 
 
 def fom(qp: QP, rho, mu, LL, sigma, x0, *, variant=INNER_AUTO, fixed=0, eps_in=1e-8,

@@ -223,6 +223,34 @@ double orc_fw_gap(const orc_qp *qp, double rho, const double *x, const double *l
   return s;
 }
 
+/* Certificate of the inner criterion eq. duquad_in: a computable upper bound
+ * on L_rho(x, mu) - d_rho(mu) = phi(x) - phi*.
+ *   sigma > 0: with x+ = [x - grad phi(x)/L]_U and g = L (x - x+),
+ *       phi(x) - phi* <= <grad phi(x), x - x+> + ||g||^2 (1/(2 sigma) - 1/(2 L))
+ *     (convexity bounds phi(x) - phi(x+); the proximal-gradient inequality for
+ *     a sigma-strongly convex, L-smooth phi bounds phi(x+) - phi*).  It is a
+ *     sum of squares-like terms, robust to rounding of the gradient.
+ *   sigma = 0: the Frank-Wolfe gap above.
+ * Reading: the paper states the criterion through the unknown d_rho(mu); any
+ * computable upper bound on it enforces eq. duquad_in. */
+double orc_inner_cert(const orc_qp *qp, double rho, const double *x, const double *lam,
+                      double LL, double sigma) {
+  if (!(sigma > 0.0)) return orc_fw_gap(qp, rho, x, lam);
+  int n = qp->n;
+  double *gr = malloc(sizeof(double) * n);
+  orc_grad_lagr(qp, rho, x, lam, gr);
+  double kappa = 1.0 / (2.0 * sigma) - 1.0 / (2.0 * LL);
+  double lin = 0.0, sq = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double xp = clampd(x[i] - gr[i] / LL, qp->lb[i], qp->ub[i]);
+    double d = x[i] - xp;
+    lin += gr[i] * d;
+    sq += (LL * d) * (LL * d);
+  }
+  free(gr);
+  return lin + sq * kappa;
+}
+
 /* ---------------------------------------------------- Algorithm FOM (inner) */
 
 /* Algorithm FOM(phi, X) of Sec. 2.1 with phi = L_rho(., mu), X = U:
@@ -233,8 +261,8 @@ double orc_fw_gap(const orc_qp *qp, double rho, const double *x, const double *l
  *   theta_{k+1} = (1 + sqrt(1 + 4 theta_k^2))/2, theta_1 = 1;
  *   FGM_sigma: beta_k = (sqrt(L) - sqrt(sigma)) / (sqrt(L) + sqrt(sigma)).
  * x holds x^0 on entry and the returned iterate on exit.
- * Stops after exactly inner_fixed iterations, or (gap mode) at the first
- * k that is a multiple of inner_check_every with FW gap(x^k) <= eps_in, or
+ * Stops after exactly inner_fixed iterations, or (certificate mode) at the
+ * first k that is a multiple of inner_check_every with cert(x^k) <= eps_in, or
  * at max_inner.  Returns the number of iterations performed.
  * phi_trace (optional, length >= cap) receives phi(x^k) for k = 1.. */
 int orc_fom(const orc_qp *qp, double rho, const double *mu, double LL, double sigma,
@@ -272,7 +300,7 @@ int orc_fom(const orc_qp *qp, double rho, const double *mu, double LL, double si
     if (inner_fixed > 0) {
       if (k >= inner_fixed) break;
     } else {
-      if (k % check_every == 0 && orc_fw_gap(qp, rho, xn, mu) <= eps_in) break;
+      if (k % check_every == 0 && orc_inner_cert(qp, rho, xn, mu, LL, sigma) <= eps_in) break;
       if (k >= max_inner) break;
     }
   }
@@ -318,7 +346,7 @@ static int lower_bound_valid(const orc_qp *qp, const orc_opts *o, const double *
  *                   mu = lambda^k for DFGM/ADFGM.
  * Stopping: fixed outer count, or the certificate read from Sec. 3.1 and the
  * epsilon-primal definition: dist_K(Gu + g) <= eps_out and F(u) - d_lb <= eps_out,
- * d_lb = max over checked outers of L_rho(ubar, mu) - gap (a lower bound of F*).
+ * d_lb = max over checked outers of L_rho(ubar, mu) - cert (a lower bound of F*).
  * trace (optional) receives ORC_TRACE_COLS values per outer iteration.      */
 int orc_dfom(const orc_qp *qp, const orc_opts *o, const double *lambda0, const double *x0,
              double *x_last, double *x_avg, double *lambda_out, orc_result *res,
@@ -396,7 +424,7 @@ int orc_dfom(const orc_qp *qp, const orc_opts *o, const double *lambda0, const d
     if (check) {
       /* lower bound from this outer's inner solution */
       if (lower_bound_valid(qp, o, mu)) {
-        double lb = orc_lagrangian(qp, rho, u, mu) - orc_fw_gap(qp, rho, u, mu);
+        double lb = orc_lagrangian(qp, rho, u, mu) - orc_inner_cert(qp, rho, u, mu, o->LL, o->sigma);
         if (lb > res->d_lb) res->d_lb = lb;
       }
       if (o->want_last) {
@@ -406,7 +434,7 @@ int orc_dfom(const orc_qp *qp, const orc_opts *o, const double *lambda0, const d
                             o->eps_in, o->inner_check_every, o->max_inner, ul, NULL, 0);
           inner_total += it2;
           if (lower_bound_valid(qp, o, lam)) {
-            double lb = orc_lagrangian(qp, rho, ul, lam) - orc_fw_gap(qp, rho, ul, lam);
+            double lb = orc_lagrangian(qp, rho, ul, lam) - orc_inner_cert(qp, rho, ul, lam, o->LL, o->sigma);
             if (lb > res->d_lb) res->d_lb = lb;
           }
         }

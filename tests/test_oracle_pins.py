@@ -382,3 +382,24 @@ def test_inner_fixed_count_bound_strongly_convex():
         kin = int(math.ceil(math.sqrt(L / s) * math.log(L * D2 / eps_in) + 1))
         x, _, _ = O.fom(qp, 0.0, mu, L, s, np.zeros(10), fixed=kin)
         assert O.lagrangian(qp, 0.0, x, mu) - phistar <= eps_in
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5])
+def test_inner_certificates_bound_suboptimality(rho):
+    """Both inner certificates (FW gap, gradient-mapping bound with sigma = lmin(Q)) are upper
+    bounds on L_rho(x, mu) - d_rho(mu), the quantity eq. duquad_in bounds by eps_in, and vanish
+    at the inner minimiser."""
+    inst, qp = _small(24, n=9, p=6, g_scale=0.02, box=0.5)
+    mu = np.abs(np.random.default_rng(3).standard_normal(6))
+    LL = inst.lmax_Q + rho * np.linalg.norm(inst.G, 2) ** 2
+    xstar, _, _ = O.fom(qp, rho, mu, LL, inst.lmin_Q, np.zeros(9), fixed=30000)
+    phistar = O.lagrangian(qp, rho, xstar, mu)
+    rng = np.random.default_rng(4)
+    for t in range(20):
+        x = np.clip(xstar + rng.standard_normal(9) * 10.0 ** -rng.uniform(0, 6), -0.5, 0.5)
+        sub = O.lagrangian(qp, rho, x, mu) - phistar
+        assert O.fw_gap(qp, rho, x, mu) >= sub - 1e-13
+        assert O.inner_cert(qp, rho, x, mu, LL, inst.lmin_Q) >= sub - 1e-13
+    assert O.inner_cert(qp, rho, xstar, mu, LL, inst.lmin_Q) < 1e-12
+    assert O.fw_gap(qp, rho, xstar, mu) < 1e-12
+    assert O.inner_cert(qp, rho, xstar, mu, LL, 0.0) == O.fw_gap(qp, rho, xstar, mu)
