@@ -193,6 +193,26 @@ dq_status dq_poll(dq_context *ctx, uint64_t ticket, double *x_last, double *x_av
                   double *lambda, dq_result *result);
 dq_status dq_serve_stop(dq_context *ctx);
 
+/* ---- measurement ----------------------------------------------------------
+ * Counters of the kernels a context launched.  With profiling enabled the
+ * grid engine brackets every inner-iteration GEMV launch (the streaming
+ * matrix pass that dominates the method, Sec. 5 "main computational
+ * bottleneck") with CUDA events on the context's stream; launches that
+ * returned early because the inner loop had already stopped are not counted.
+ * gemv_bytes counts each matrix element once plus the vectors read and
+ * written once (the algorithmic bytes of those launches). */
+typedef struct {
+  int64_t launches;       /* all kernels launched by this context            */
+  int64_t gemv_launches;  /* timed inner-iteration GEMV launches             */
+  double gemv_ms;         /* their summed device time                        */
+  double gemv_bytes;      /* their algorithmic bytes                         */
+} dq_stats;
+
+/* enable != 0 turns per-launch event timing of the GEMV on. */
+dq_status dq_context_profile(dq_context *ctx, int32_t enable);
+/* Copy the counters; reset != 0 zeroes them afterwards. */
+dq_status dq_context_stats(dq_context *ctx, dq_stats *out, int32_t reset);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *dq_last_error(void);
 

@@ -300,3 +300,6 @@ def k_out(alg: int, eps: float, Ld: float, Rd: float) -> float:
     """Outer iteration count of eq. choose_ein."""
     v = 8.0 * Ld * Rd * Rd / eps
     return v if alg in (DGM, ADGM) else math.sqrt(v)
+
+
+from .sampled import sampled_fom_step  # noqa: E402,F401

@@ -1,0 +1,595 @@
+// cta_engine.cuh -- whole-solve-per-thread-block engine.
+//
+// One CTA runs the complete Algorithm DFOM (arXiv 1504.05708, Sec. 3) for one
+// QP instance: every inner Algorithm FOM iteration (Sec. 2.1), every dual
+// update, the primal averaging (eq. average_primal), the last-iterate solve
+// (eq. last_primal) and the stopping certificate, without returning to the
+// host.  A persistent grid pulls instances from a device work queue, so one
+// launch solves a batch of instances of different sizes and algorithms.
+//
+// Data layout: vectors live in shared memory; Q (n x n), G (p x n) and its
+// transpose GT (n x p), row-major, are staged into shared memory when they
+// fit and read through L2 otherwise.  Every matrix-vector product is written
+// as out = M' v with one thread per output column, so each step of the
+// reduction loop is a coalesced row read of M, and the summation order is
+// fixed (results do not depend on which CTA runs the instance or what else
+// is in the batch).
+//
+// Inner iteration in "x-side" form: the gradient of L_rho(., mu) at
+// y = x^k + beta (x^k - x^{k-1}) needs Q y and G y, which are linear in y, so
+// Q x^k and G x^k are carried and Q y = Q x^k + beta (Q x^k - Q x^{k-1}).  The
+// matrix products per iteration are Q x^k, G x^k and G' w (rho > 0) or Q x^k
+// alone (rho = 0, with c = q + G' mu formed once per outer iteration, the
+// precomputation the paper's bottleneck section describes), and the gradient
+// at x^k for the stopping certificate comes for free when rho = 0.
+#pragma once
+#include "dq_common.cuh"
+
+namespace dq {
+
+template <typename T>
+struct CtaInst {
+  int n, p, cone, alg;
+  const T *Q, *G, *GT;            // device matrices
+  const T *q, *g, *lb, *ub;       // device vectors
+  double lmax_Q, lmin_Q, normG2;  // NaN lmax_Q / normG2: power iteration on chip
+  double rho;                     // NaN: 0 for DGM/DFGM, 1/||G||^2 for ADGM/ADFGM
+  double LL, sigma, Ld;           // NaN: derived (Sec. 3 Step 1, eq. Ld)
+  int inner_fixed, inner_check_every, max_inner;
+  double eps_in;
+  int outer_fixed, check_every, max_outer;
+  double eps_out;
+  int want_last, want_avg, kd_plus;
+  const T *x0, *lam0;             // warm start (nullable)
+  T *x_state, *lam_state;         // final ubar^k and lambda^k (nullable)
+  T *x_last, *x_avg, *lam_out;    // outputs (nullable)
+  DevResult *res;
+  double *consts_out;             // nullable: lmax_Q, normG2, LL, Ld, sigma, rho
+};
+
+// out[i] = sum_j M[j*ld + i] v[j], i < cols, j < rows  (out = M' v).
+// One thread per output, four independent accumulators, fixed order.
+template <typename A, typename T, typename V>
+__device__ __forceinline__ void mtv(const T* __restrict__ M, int rows, int cols, int ld,
+                                    const V* __restrict__ v, A* __restrict__ out) {
+  for (int i = threadIdx.x; i < cols; i += blockDim.x) {
+    const T* col = M + i;
+    A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0);
+    int j = 0;
+    for (; j + 4 <= rows; j += 4) {
+      a0 += A(col[(size_t)(j + 0) * ld]) * A(v[j + 0]);
+      a1 += A(col[(size_t)(j + 1) * ld]) * A(v[j + 1]);
+      a2 += A(col[(size_t)(j + 2) * ld]) * A(v[j + 2]);
+      a3 += A(col[(size_t)(j + 3) * ld]) * A(v[j + 3]);
+    }
+    for (; j < rows; ++j) a0 += A(col[(size_t)j * ld]) * A(v[j]);
+    out[i] = (a0 + a1) + (a2 + a3);
+  }
+}
+
+// Same product with the accurate accumulator of the element type (FP64 or Dot2).
+template <typename T>
+__device__ __forceinline__ void mtv_acc(const T* __restrict__ M, int rows, int cols, int ld,
+                                        const T* __restrict__ v, double* __restrict__ out) {
+  using Acc = typename AccurateAcc<T>::type;
+  for (int i = threadIdx.x; i < cols; i += blockDim.x) {
+    const T* col = M + i;
+    Acc a;
+    for (int j = 0; j < rows; ++j) a.add(col[(size_t)j * ld], v[j]);
+    out[i] = a.get();
+  }
+}
+
+template <typename T>
+struct XState {  // three rotating buffers each for x, Q x, G x
+  T *x, *xp, *xn;
+  T *Qx, *Qxp, *Qxn;
+  T *Gx, *Gxp, *Gxn;
+};
+
+template <typename T>
+struct CtaWs {
+  XState<T> A, B;        // main warm-start chain, extra last-iterate solve
+  T *c, *tn, *w, *mu, *lam, *lamp, *ul, *uavg;
+  double *usum, *dn, *dp, *red;
+  const T *Q, *G, *GT;
+};
+
+template <typename T>
+__device__ __forceinline__ void vcopy(T* __restrict__ d, const T* __restrict__ s, int m) {
+  for (int i = threadIdx.x; i < m; i += blockDim.x) d[i] = s[i];
+}
+
+// Certificate of eq. duquad_in at x (x, Q x, G x given): upper bound on
+// L_rho(x, mu) - d_rho(mu).  sigma > 0: gradient-mapping bound
+// <grad, x - x+> + ||L (x - x+)||^2 (1/(2 sigma) - 1/(2 L)); sigma = 0:
+// Frank-Wolfe gap.  rho = 0 uses c = q + G' mu; rho > 0 forms G' w(x).
+template <typename T>
+__device__ double cta_cert(const CtaInst<T>& I, CtaWs<T>& W, const T* x, const T* Qx, const T* Gx,
+                           const T* mu, bool c_valid) {
+  const int n = I.n, p = I.p;
+  const bool aug = I.rho > 0.0;
+  const T rho = T(I.rho);
+  if (aug) {
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+      T v = mu[j] + rho * (Gx[j] + I.g[j]);
+      W.w[j] = I.cone == CONE_EQ ? v : (v > T(0) ? v : T(0));
+    }
+    __syncthreads();
+    mtv<T>(W.G, p, n, n, W.w, W.tn);
+    __syncthreads();
+  } else if (!c_valid) {
+    mtv<T>(W.G, p, n, n, mu, W.tn);
+    __syncthreads();
+  }
+  const double L = I.LL, sg = I.sigma;
+  const double kap = sg > 0.0 ? 1.0 / (2.0 * sg) - 1.0 / (2.0 * L) : 0.0;
+  double part = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    T gr = aug ? (Qx[i] + I.q[i] + W.tn[i]) : (c_valid ? Qx[i] + W.c[i] : Qx[i] + I.q[i] + W.tn[i]);
+    const double gd = double(gr), xd = double(x[i]);
+    if (sg > 0.0) {
+      const double xp = fmin(fmax(xd - gd / L, double(I.lb[i])), double(I.ub[i]));
+      const double d = xd - xp;
+      part += gd * d + (L * d) * (L * d) * kap;
+    } else {
+      const double a = gd * double(I.lb[i]), b = gd * double(I.ub[i]);
+      part += gd * xd - (a < b ? a : b);
+    }
+  }
+  return block_sum(part, W.red);
+}
+
+// Algorithm FOM on phi = L_rho(., mu) over the box, warm-started from S.x
+// (with S.Qx and, for rho > 0, S.Gx valid).  On return S.x = ubar, S.Qx = Q ubar,
+// S.Gx = G ubar.  Inner variant: FGM_sigma when sigma > 0, else FGM.
+template <typename T>
+__device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* mu) {
+  const int n = I.n, p = I.p;
+  const bool aug = I.rho > 0.0;
+  const T rho = T(I.rho), L = T(I.LL);
+  if (!aug) {  // c = q + G' mu, fixed over the inner loop
+    if (p > 0) {
+      mtv<T>(W.G, p, n, n, mu, W.c);
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) W.c[i] = (p > 0 ? W.c[i] : T(0)) + I.q[i];
+  }
+  vcopy(S.xp, S.x, n);
+  vcopy(S.Qxp, S.Qx, n);
+  if (aug) vcopy(S.Gxp, S.Gx, p);
+  __syncthreads();
+  const bool fgm_sigma = I.sigma > 0.0;
+  const double beta_sigma = (sqrt(I.LL) - sqrt(I.sigma)) / (sqrt(I.LL) + sqrt(I.sigma));
+  double theta = 1.0, beta = 0.0;
+  const int m = I.inner_check_every > 0 ? I.inner_check_every : 1;
+  int k = 0;
+  for (;;) {
+    ++k;
+    const T b = T(beta);
+    if (aug) {  // w = [mu + rho (G y + g)]_+ ,  tn = G' w
+      for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        const T Gy = S.Gx[j] + b * (S.Gx[j] - S.Gxp[j]);
+        const T v = mu[j] + rho * (Gy + I.g[j]);
+        W.w[j] = I.cone == CONE_EQ ? v : (v > T(0) ? v : T(0));
+      }
+      __syncthreads();
+      mtv<T>(W.G, p, n, n, W.w, W.tn);
+      __syncthreads();
+    }
+    // step 1 of FOM: x^k = [y - grad phi(y) / L]_U
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const T y = S.x[i] + b * (S.x[i] - S.xp[i]);
+      const T Qy = S.Qx[i] + b * (S.Qx[i] - S.Qxp[i]);
+      const T gr = aug ? Qy + I.q[i] + W.tn[i] : Qy + W.c[i];
+      S.xn[i] = clampT(y - gr / L, I.lb[i], I.ub[i]);
+    }
+    __syncthreads();
+    mtv<T>(W.Q, n, n, n, S.xn, S.Qxn);
+    if (aug) mtv<T>(W.GT, n, p, p, S.xn, S.Gxn);
+    __syncthreads();
+    // step 2 weight beta_k (GM/FGM/FGM_sigma rules, Sec. 2.1)
+    if (fgm_sigma) {
+      beta = beta_sigma;
+    } else {
+      const double tn1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+      beta = (theta - 1.0) / tn1;
+      theta = tn1;
+    }
+    T* t;
+    t = S.xp; S.xp = S.x; S.x = S.xn; S.xn = t;
+    t = S.Qxp; S.Qxp = S.Qx; S.Qx = S.Qxn; S.Qxn = t;
+    if (aug) { t = S.Gxp; S.Gxp = S.Gx; S.Gx = S.Gxn; S.Gxn = t; }
+    if (I.inner_fixed > 0) {
+      if (k >= I.inner_fixed) break;
+    } else {
+      if (k % m == 0) {
+        const double cert = cta_cert(I, W, S.x, S.Qx, S.Gx, mu, !aug);
+        if (cert <= I.eps_in) break;
+      }
+      if (k >= I.max_inner) break;
+    }
+  }
+  if (!aug && p > 0) {  // G ubar for the dual gradient
+    mtv<T>(W.GT, n, p, p, S.x, S.Gx);
+    __syncthreads();
+  }
+  return k;
+}
+
+// FP64-accurate evaluation at u: F(u), dist_K(Gu + g) and, when mu is given,
+// L_rho(u, mu) (eq. auglag1) and the inner certificate at (u, mu).
+struct EvalOut {
+  double F, infeas, lagr, cert;
+};
+
+template <typename T>
+__device__ EvalOut cta_eval(const CtaInst<T>& I, CtaWs<T>& W, const T* u, const T* mu) {
+  const int n = I.n, p = I.p;
+  mtv_acc<T>(W.Q, n, n, n, u, W.dn);
+  if (p > 0) mtv_acc<T>(W.GT, n, p, p, u, W.dp);
+  __syncthreads();
+  double pf = 0.0, pi = 0.0, pl = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    pf += 0.5 * double(u[i]) * W.dn[i] + double(I.q[i]) * double(u[i]);
+  const double rho = I.rho;
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const double r = W.dp[j] + double(I.g[j]);
+    const double d = r - proj_K(I.cone, r);
+    pi += d * d;
+    if (mu) {
+      const double mj = double(mu[j]);
+      if (rho > 0.0) {
+        const double z = r + mj / rho;
+        const double dz = z - proj_K(I.cone, z);
+        pl += 0.5 * rho * dz * dz - mj * mj / (2.0 * rho);
+      } else {
+        pl += mj * r;
+      }
+    }
+  }
+  EvalOut e;
+  e.F = block_sum(pf, W.red);
+  e.infeas = sqrt(block_sum(pi, W.red));
+  e.lagr = e.cert = NAN;
+  if (!mu) return e;
+  e.lagr = e.F + block_sum(pl, W.red);
+  // gradient of L_rho(., mu) at u, accumulated accurately
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const double r = W.dp[j] + double(I.g[j]);
+    const double mj = double(mu[j]);
+    double w;
+    if (rho > 0.0) {
+      const double z = r + mj / rho;
+      w = rho * (z - proj_K(I.cone, z));
+    } else {
+      w = mj;
+    }
+    W.dp[j] = w;
+  }
+  __syncthreads();
+  using Acc = typename AccurateAcc<T>::type;
+  const double L = I.LL, sg = I.sigma;
+  const double kap = sg > 0.0 ? 1.0 / (2.0 * sg) - 1.0 / (2.0 * L) : 0.0;
+  double pc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double gsum;
+    if (sizeof(T) == 8) {
+      double a = 0.0;
+      for (int j = 0; j < p; ++j) a = fma(double(W.G[(size_t)j * n + i]), W.dp[j], a);
+      gsum = a;
+    } else {
+      Acc a;
+      for (int j = 0; j < p; ++j) {
+        // split the FP64 weight into two floats so the product stays accurate
+        const float hi = float(W.dp[j]);
+        const float lo = float(W.dp[j] - double(hi));
+        a.add(float(W.G[(size_t)j * n + i]), hi);
+        a.add(float(W.G[(size_t)j * n + i]), lo);
+      }
+      gsum = a.get();
+    }
+    const double gd = W.dn[i] + double(I.q[i]) + gsum;
+    const double xd = double(u[i]);
+    if (sg > 0.0) {
+      const double xp = fmin(fmax(xd - gd / L, double(I.lb[i])), double(I.ub[i]));
+      const double d = xd - xp;
+      pc += gd * d + (L * d) * (L * d) * kap;
+    } else {
+      const double a = gd * double(I.lb[i]), b = gd * double(I.ub[i]);
+      pc += gd * xd - (a < b ? a : b);
+    }
+  }
+  e.cert = block_sum(pc, W.red);
+  return e;
+}
+
+// lambda_max of Q (which = 0) or of G'G (which = 1, i.e. ||G||^2) by power
+// iteration from the normalised all-ones vector.  Products in T, norms and
+// the Rayleigh quotient theta in FP64.  Returns theta + ||A v - theta v||, an
+// upper estimate once v lies in the top eigenspace; stops when the residual
+// is below rtol * theta or after max_it steps.
+template <typename T>
+__device__ double cta_power(const CtaInst<T>& I, CtaWs<T>& W, int which, int max_it, double rtol) {
+  const int n = I.n, p = I.p;
+  T* v = W.A.x;
+  T* w = W.A.Qx;
+  T* t = W.A.Gx;
+  const T v0 = T(1.0 / sqrt(double(n)));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = v0;
+  __syncthreads();
+  double theta = 0.0, r = 0.0;
+  for (int it = 0; it < max_it; ++it) {
+    if (which == 0) {
+      mtv<T>(W.Q, n, n, n, v, w);
+    } else {
+      mtv<T>(W.GT, n, p, p, v, t);
+      __syncthreads();
+      mtv<T>(W.G, p, n, n, t, w);
+    }
+    __syncthreads();
+    double pvw = 0.0, pww = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      pvw += double(v[i]) * double(w[i]);
+      pww += double(w[i]) * double(w[i]);
+    }
+    const double vw = block_sum(pvw, W.red);
+    const double ww = block_sum(pww, W.red);
+    theta = vw;
+    r = sqrt(fmax(ww - vw * vw, 0.0));
+    if (ww == 0.0 || (it >= 3 && r <= rtol * theta)) break;
+    const double inv = 1.0 / sqrt(ww);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = T(double(w[i]) * inv);
+    __syncthreads();
+  }
+  __syncthreads();
+  return theta + r;
+}
+
+__device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+// Shared-memory bytes for the vectors of an (n, p) instance.
+template <typename T>
+__host__ __device__ inline size_t cta_vec_bytes(int n, int p) {
+  const size_t pn = p > 0 ? p : 1;
+  auto a16 = [](size_t b) { return (b + 15) & ~size_t(15); };
+  size_t b = a16(40 * sizeof(double));
+  b += 2 * a16(n * sizeof(double)) + a16(pn * sizeof(double));  // usum, dn, dp
+  b += 2 * (6 * a16(n * sizeof(T)) + 3 * a16(pn * sizeof(T)));  // A, B states
+  b += 4 * a16(n * sizeof(T));                                   // c, tn, ul, uavg
+  b += 4 * a16(pn * sizeof(T));                                  // w, mu, lam, lamp
+  return b;
+}
+template <typename T>
+__host__ __device__ inline size_t cta_mat_bytes(int n, int p) {
+  return ((size_t)n * n + 2 * (size_t)n * p) * sizeof(T) + 64;
+}
+
+template <typename T>
+__device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes) {
+  const int n = I.n, p = I.p;
+  const size_t pn = p > 0 ? p : 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> unsigned char* {
+    unsigned char* ptr = smem + off;
+    off += align16(bytes);
+    return ptr;
+  };
+  CtaWs<T> W;
+  W.red = (double*)take(40 * sizeof(double));
+  W.usum = (double*)take(n * sizeof(double));
+  W.dn = (double*)take(n * sizeof(double));
+  W.dp = (double*)take(pn * sizeof(double));
+  XState<T>* st[2] = {&W.A, &W.B};
+  for (int s = 0; s < 2; ++s) {
+    XState<T>& S = *st[s];
+    S.x = (T*)take(n * sizeof(T)); S.xp = (T*)take(n * sizeof(T)); S.xn = (T*)take(n * sizeof(T));
+    S.Qx = (T*)take(n * sizeof(T)); S.Qxp = (T*)take(n * sizeof(T)); S.Qxn = (T*)take(n * sizeof(T));
+    S.Gx = (T*)take(pn * sizeof(T)); S.Gxp = (T*)take(pn * sizeof(T)); S.Gxn = (T*)take(pn * sizeof(T));
+  }
+  W.c = (T*)take(n * sizeof(T));
+  W.tn = (T*)take(n * sizeof(T));
+  W.ul = (T*)take(n * sizeof(T));
+  W.uavg = (T*)take(n * sizeof(T));
+  W.w = (T*)take(pn * sizeof(T));
+  W.mu = (T*)take(pn * sizeof(T));
+  W.lam = (T*)take(pn * sizeof(T));
+  W.lamp = (T*)take(pn * sizeof(T));
+  W.Q = I.Q; W.G = I.G; W.GT = I.GT;
+  // stage the matrices in shared memory when they fit
+  const size_t nn = (size_t)n * n, np_ = (size_t)n * p;
+  if (off + cta_mat_bytes<T>(n, p) <= smem_bytes) {
+    T* Qs = (T*)take(nn * sizeof(T));
+    T* Gs = (T*)take(np_ * sizeof(T));
+    T* GTs = (T*)take(np_ * sizeof(T));
+    for (size_t i = threadIdx.x; i < nn; i += blockDim.x) Qs[i] = I.Q[i];
+    for (size_t i = threadIdx.x; i < np_; i += blockDim.x) { Gs[i] = I.G[i]; GTs[i] = I.GT[i]; }
+    W.Q = Qs; W.G = Gs; W.GT = GTs;
+  }
+  __syncthreads();
+  // FP64 constants (a1): lambda_max(Q), ||G||^2, then L_L, sigma_L, L_d, rho
+  if (isnan(I.lmax_Q)) I.lmax_Q = cta_power<T>(I, W, 0, 300, 1e-3);
+  if (isnan(I.normG2)) I.normG2 = p > 0 ? cta_power<T>(I, W, 1, 300, 1e-3) : 0.0;
+  const double lmin = isnan(I.lmin_Q) ? 0.0 : I.lmin_Q;
+  if (isnan(I.rho)) I.rho = (I.alg == ALG_ADGM || I.alg == ALG_ADFGM) ? (I.normG2 > 0.0 ? 1.0 / I.normG2 : 1.0) : 0.0;
+  if (isnan(I.LL)) I.LL = I.lmax_Q + I.rho * I.normG2;
+  if (isnan(I.sigma)) I.sigma = lmin;
+  if (isnan(I.Ld)) {
+    const double den = lmin + I.rho * I.normG2;
+    I.Ld = I.normG2 > 0.0 ? (den > 0.0 ? I.normG2 / den : INFINITY) : 1.0;
+  }
+  if (isnan(I.eps_in))  // eq. choose_ein with R_d = 1
+    I.eps_in = (I.alg == ALG_DGM || I.alg == ALG_ADGM) ? I.eps_out / 4.0
+                                                       : I.eps_out * sqrt(I.eps_out) / (8.0 * sqrt(2.0 * I.Ld));
+  if (threadIdx.x == 0 && I.consts_out) {
+    I.consts_out[0] = I.lmax_Q; I.consts_out[1] = I.normG2; I.consts_out[2] = I.LL;
+    I.consts_out[3] = I.Ld; I.consts_out[4] = I.sigma; I.consts_out[5] = I.rho;
+  }
+  if (!(I.Ld < INFINITY) || !(I.LL > 0.0)) {  // DGM/DFGM need lambda_min(Q) > 0 (Case 1)
+    if (threadIdx.x == 0 && I.res) {
+      DevResult r = {};
+      r.status = -1;
+      r.f_last = r.infeas_last = r.f_avg = r.infeas_avg = r.d_lb = NAN;
+      *I.res = r;
+    }
+    __syncthreads();
+    return;
+  }
+  // initial point and multipliers (Algorithm DFOM: lambda^0 = mu^1 in K_d)
+  XState<T>& A = W.A;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    A.x[i] = I.x0 ? I.x0[i] : clampT(T(0), I.lb[i], I.ub[i]);
+    W.usum[i] = 0.0;
+  }
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const T l0 = I.lam0 ? I.lam0[j] : T(0);
+    W.lam[j] = l0; W.lamp[j] = l0; W.mu[j] = l0;
+  }
+  __syncthreads();
+  mtv<T>(W.Q, n, n, n, A.x, A.Qx);
+  if (p > 0) mtv<T>(W.GT, n, p, p, A.x, A.Gx);
+  __syncthreads();
+
+  const bool aug = I.rho > 0.0, fast = alg_fast(I.alg);
+  const T alpha = T(1.0 / (2.0 * I.Ld));
+  const T rho = T(I.rho);
+  double theta = 1.0, S = 0.0;
+  long long inner_total = 0;
+  const int check_every = I.check_every > 0 ? I.check_every : 1;
+  const int kmax = I.outer_fixed > 0 ? I.outer_fixed : I.max_outer;
+  double d_lb = -INFINITY, f_last = NAN, i_last = NAN, f_avg = NAN, i_avg = NAN;
+  int conv_last = 0, conv_avg = 0, status = ST_OK, k = 0;
+  bool done = false, last_valid = false;
+
+  while (k < kmax && !done) {
+    ++k;
+    // Step 1: ubar^k = FOM(L_rho(., mu^k), U), warm start ubar^{k-1}
+    inner_total += cta_fom(I, W, A, W.mu);
+    // Step 2: lambda^k = [mu^k + (G ubar + g - s(ubar, mu))/(2 L_d)]_{K_d}
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+      const T r = A.Gx[j] + I.g[j];
+      const T s = aug ? proj_K(I.cone, r + W.mu[j] / rho) : T(0);
+      W.lam[j] = proj_Kd(I.cone, I.kd_plus != 0, W.mu[j] + alpha * (r - s));
+    }
+    // averaging weight theta_k (eq. average_primal)
+    S += theta;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) W.usum[i] += theta * double(A.x[i]);
+    double beta = 0.0;
+    if (fast) {
+      const double tn1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+      beta = (theta - 1.0) / tn1;
+      theta = tn1;
+    }
+    __syncthreads();
+    const bool final_iter = (k == kmax);
+    if (final_iter || (I.outer_fixed <= 0 && k % check_every == 0)) {
+      bool mu_ok = aug || I.cone == CONE_EQ;
+      if (!mu_ok) {
+        int neg = 0;
+        for (int j = threadIdx.x; j < p; j += blockDim.x) neg |= (W.mu[j] < T(0));
+        mu_ok = !__syncthreads_or(neg);
+      }
+      if (mu_ok) {
+        EvalOut e = cta_eval(I, W, A.x, W.mu);
+        d_lb = fmax(d_lb, e.lagr - e.cert);
+      }
+      if (I.want_last) {
+        if (fast) {  // ubar(lambda^k): extra warm-started inner solve at mu = lambda^k
+          XState<T>& B = W.B;
+          vcopy(B.x, A.x, n);
+          vcopy(B.Qx, A.Qx, n);
+          if (p > 0) vcopy(B.Gx, A.Gx, p);
+          __syncthreads();
+          inner_total += cta_fom(I, W, B, W.lam);
+          vcopy(W.ul, B.x, n);
+          __syncthreads();
+          bool lam_ok = aug || I.cone == CONE_EQ;
+          if (!lam_ok) {
+            int neg = 0;
+            for (int j = threadIdx.x; j < p; j += blockDim.x) neg |= (W.lam[j] < T(0));
+            lam_ok = !__syncthreads_or(neg);
+          }
+          if (lam_ok) {
+            EvalOut e = cta_eval(I, W, W.ul, W.lam);
+            d_lb = fmax(d_lb, e.lagr - e.cert);
+          }
+        } else {
+          vcopy(W.ul, A.x, n);
+          __syncthreads();
+        }
+        EvalOut e = cta_eval(I, W, W.ul, (const T*)nullptr);
+        f_last = e.F;
+        i_last = e.infeas;
+        last_valid = true;
+      }
+      if (I.want_avg) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) W.uavg[i] = T(W.usum[i] / S);
+        __syncthreads();
+        EvalOut e = cta_eval(I, W, W.uavg, (const T*)nullptr);
+        f_avg = e.F;
+        i_avg = e.infeas;
+      }
+      if ((I.want_last && !(isfinite(f_last) && isfinite(i_last))) ||
+          (I.want_avg && !(isfinite(f_avg) && isfinite(i_avg)))) {
+        status = ST_NONFINITE;
+        done = true;
+      }
+      if (I.outer_fixed <= 0 && !done) {
+        conv_last = I.want_last && i_last <= I.eps_out && f_last - d_lb <= I.eps_out;
+        conv_avg = I.want_avg && i_avg <= I.eps_out && f_avg - d_lb <= I.eps_out;
+        done = conv_last || conv_avg;
+      }
+    }
+    // Step 3: mu^{k+1} = lambda^k + beta_k (lambda^k - lambda^{k-1})
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+      const T l = W.lam[j];
+      const T mm = l + T(beta) * (l - W.lamp[j]);
+      W.lamp[j] = l;
+      W.mu[j] = mm;
+    }
+    __syncthreads();
+  }
+  if (!last_valid) {
+    vcopy(W.ul, A.x, n);
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (I.x_last) I.x_last[i] = W.ul[i];
+    if (I.x_avg) I.x_avg[i] = T(W.usum[i] / S);
+    if (I.x_state) I.x_state[i] = A.x[i];
+  }
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    if (I.lam_out) I.lam_out[j] = W.lam[j];
+    if (I.lam_state) I.lam_state[j] = W.lam[j];
+  }
+  if (threadIdx.x == 0 && I.res) {
+    DevResult r;
+    r.status = status != ST_OK ? status : ((I.outer_fixed > 0 || conv_last || conv_avg) ? ST_OK : ST_NOT_CONVERGED);
+    r.outer_iters = k;
+    r.inner_iters = inner_total;
+    r.converged_last = conv_last;
+    r.converged_avg = conv_avg;
+    r.f_last = f_last; r.infeas_last = i_last; r.f_avg = f_avg; r.infeas_avg = i_avg; r.d_lb = d_lb;
+    *I.res = r;
+  }
+  __syncthreads();
+}
+
+// Persistent kernel: CTAs pull instance indices (in `order`) from a device counter.
+template <typename T>
+__global__ void __launch_bounds__(256) cta_solve_kernel(const CtaInst<T>* __restrict__ insts,
+                                                        const int* __restrict__ order, int count,
+                                                        int* __restrict__ next, size_t smem_bytes) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_idx;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(next, 1);
+    __syncthreads();
+    const int idx = s_idx;
+    __syncthreads();
+    if (idx >= count) break;
+    CtaInst<T> I = insts[order ? order[idx] : idx];
+    cta_solve<T>(I, smem, smem_bytes);
+  }
+}
+
+}  // namespace dq

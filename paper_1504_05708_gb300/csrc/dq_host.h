@@ -1,0 +1,84 @@
+// dq_host.h -- host-side handle definitions shared by the C-ABI translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "duquad.h"
+#include "dq_common.cuh"
+
+namespace dq {
+
+void set_error(const char* fmt, ...);
+
+#define DQ_CK(call)                                                             \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess) {                                                    \
+      ::dq::set_error("%s failed: %s", #call, cudaGetErrorString(e_));          \
+      return DQ_ERR_CUDA;                                                       \
+    }                                                                           \
+  } while (0)
+
+struct GridWs;   // large-instance engine workspace (grid_engine.cu)
+struct TcWs;     // tensor-core batch workspace (tc_engine.cu)
+struct ServeState;
+
+// Resolved solve options (defaults applied; NaN kept where the device derives).
+struct SolveCfg {
+  int alg, output, inner_stop, engine;
+  double eps_out, eps_in, rho;
+  int fixed_outer, fixed_inner, max_outer, max_inner, check_every, inner_check_every;
+  int warm_start, kd_literal;
+  double Ld, LL, sigma;
+};
+
+}  // namespace dq
+
+struct dq_context {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  // grow-only scratch for per-call device arrays
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  dq::ServeState* serve = nullptr;
+  // measurement
+  int64_t launches = 0;
+  bool profile = false;
+  int64_t gemv_launches = 0;
+  double gemv_ms = 0.0, gemv_bytes = 0.0;
+};
+
+struct dq_problem {
+  dq_context* ctx = nullptr;
+  int n = 0, p = 0, batch = 1, cone = 0, prec = 0;
+  size_t esz = 8;                  // element size of the device arrays
+  void *Q = nullptr, *G = nullptr, *GT = nullptr;
+  bool own_Q = false, own_G = false;
+  void *q = nullptr, *g = nullptr, *lb = nullptr, *ub = nullptr;
+  void *x_state = nullptr, *lam_state = nullptr;
+  bool has_state = false;
+  double lmax_Q = NAN, lmin_Q = NAN, normG2 = NAN;
+  dq::GridWs* gws = nullptr;
+  dq::TcWs* tws = nullptr;
+  std::mutex mu;
+};
+
+namespace dq {
+dq_status resolve_opts(const dq_problem* prob, const dq_solve_opts* o, SolveCfg* c);
+dq_status ctx_scratch(dq_context* ctx, size_t bytes, void** out);
+dq_status grid_solve(dq_problem* prob, const SolveCfg& c, const dq_outputs* out, dq_result* res);
+void grid_free(GridWs* w);
+dq_status grid_constants(dq_problem* prob);
+dq_status tc_solve(dq_problem* prob, const SolveCfg& c, const dq_outputs* out, dq_result* res);
+void tc_free(TcWs* w);
+dq_status cta_solve_problems(dq_problem* const* probs, int count, const SolveCfg* cfgs,
+                             const dq_outputs* outs, dq_result* results, int smem_cap,
+                             int threads);
+void fill_result(dq_result* r, const DevResult& d, const double* consts, const SolveCfg& c);
+}  // namespace dq

@@ -1,0 +1,914 @@
+// grid_engine.cu -- one large QP instance spread over the whole GPU.
+//
+// Algorithm DFOM (arXiv 1504.05708, Sec. 3) around Algorithm FOM (Sec. 2.1)
+// for a single dense instance too large for one CTA (n = 20000, p = 10000 is
+// the target size: Q is 1.6 GB, G 0.8 GB in FP32).  The paper's bottleneck
+// section identifies the matrix-vector products as the whole cost, so every
+// inner iteration is one or two streaming passes over the matrices, each a
+// row-dot GEMV that reads every matrix element exactly once from HBM with
+// 16-byte loads:
+//   rho = 0 : one pass over Q         (x^k -> Q x^k; c = q + G' mu per outer)
+//   rho > 0 : a pass over G' (n x p)  (w(y) = [mu + rho (G y + g)]_+ -> G' w)
+//             and a pass over [Q; G]  (x^k -> Q x^k, G x^k)
+// G' is a transposed copy kept by the problem store so both G y and G' w are
+// row dots (no cross-CTA partial sums).  The vector each pass needs (the new
+// iterate x^k = [y - grad/L]_U, or w) is formed in the kernel's prologue from
+// the carried vectors into shared memory, so an inner iteration is one kernel
+// (rho = 0) or two (rho > 0).  Row dots accumulate float products in short
+// FMA chains folded into a compensated (Kahan) float pair, then combine lanes
+// in FP64, which keeps the gradient accurate enough for the stopping
+// certificate at n = 20000.
+//
+// Control stays on the device: the certificate kernel sets a "done" flag
+// that every later step kernel checks on entry, so the host can queue the
+// next chunk of iterations before it learns whether the current one stopped
+// (the GPU never waits for the host inside an inner solve).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "dq_host.h"
+
+namespace dq {
+
+// ------------------------------------------------------------------ kernels
+
+template <typename T> struct V16;
+template <> struct V16<float> { using type = float4; static constexpr int E = 4; };
+template <> struct V16<double> { using type = double2; static constexpr int E = 2; };
+
+__device__ __forceinline__ float vdot(const float4& a, const float4& b) {
+  float s = a.x * b.x;
+  s = fmaf(a.y, b.y, s);
+  s = fmaf(a.z, b.z, s);
+  return fmaf(a.w, b.w, s);
+}
+__device__ __forceinline__ double vdot(const double2& a, const double2& b) { return fma(a.y, b.y, a.x * b.x); }
+
+template <typename T>
+__device__ __forceinline__ typename V16<T>::type ldg_stream(const typename V16<T>::type* p) {
+  return __ldcs(p);  // streaming load: the matrices are read once per pass
+}
+
+struct Ctrl {          // device control block of the grid engine
+  int inner_done;      // set by the certificate kernel
+  int k_stop;          // iteration at which the inner loop stopped
+  unsigned int arrive; // last-block counter of the reductions
+  int pad;
+  double cert;
+  double sums[8];      // results of the reduction kernels
+};
+
+enum { VM_COPY = 0, VM_STEP = 1, VM_W = 2, VM_COPY2 = 3 };
+
+template <typename T>
+struct RowJob {
+  const T* M1; int R1; const T* M2; int R2; int cols;
+  T* out1; T* out2;            // T outputs (fast mode)
+  double* dout1; double* dout2; // FP64 outputs (accurate mode)
+  const T* add1;               // optional per-row addend of the M1 rows
+  int vmode;
+  const T *a0, *a1, *a2, *a3, *a4, *a5, *a6, *a7;
+  T beta, L, rho;
+  int cone;
+  T* vout;                     // where CTAs store their slice of the prologue vector
+  const int* done;             // non-null: return at once when *done != 0
+};
+
+// Prologue: the vector v (length len) in shared memory.
+template <typename T>
+__device__ __forceinline__ void form_vector(const RowJob<T>& J, T* v, int len) {
+  const T b = J.beta;
+  const int chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * chunk, hi = min(len, lo + chunk);
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    T val;
+    if (J.vmode == VM_STEP) {  // x^k = [y - (Q y + add) / L]_U
+      const T x = J.a0[i], xp = J.a1[i], qx = J.a2[i], qxp = J.a3[i];
+      const T y = x + b * (x - xp);
+      const T qy = qx + b * (qx - qxp);
+      const T gr = qy + J.a4[i] + (J.a5 ? J.a5[i] : T(0));
+      const T t = y - gr / J.L;
+      val = t < J.a6[i] ? J.a6[i] : (t > J.a7[i] ? J.a7[i] : t);
+    } else if (J.vmode == VM_W) {  // w = [mu + rho (G y + g)]_K*
+      const T gx = J.a0[i], gxp = J.a1[i];
+      const T gy = gx + b * (gx - gxp);
+      const T t = J.a2[i] + J.rho * (gy + J.a3[i]);
+      val = J.cone == CONE_EQ ? t : (t > T(0) ? t : T(0));
+    } else {
+      val = J.a0[i];
+    }
+    v[i] = val;
+    if (J.vout && i >= lo && i < hi) J.vout[i] = val;
+  }
+}
+
+// Row-dot GEMV over the rows of M1 then M2 with the prologue vector.  One
+// warp per row; ACC = true gives Dot2-accurate FP64 outputs.
+template <typename T, bool ACC>
+__global__ void __launch_bounds__(512) k_rows(RowJob<T> J) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (J.done && *(volatile const int*)J.done) return;
+  T* v = (T*)smem_raw;
+  form_vector<T>(J, v, J.cols);
+  __syncthreads();
+  using V = typename V16<T>::type;
+  constexpr int E = V16<T>::E;
+  const int lane = threadIdx.x & 31;
+  const int warps = blockDim.x >> 5;
+  const int gw = blockIdx.x * warps + (threadIdx.x >> 5);
+  const int tw = gridDim.x * warps;
+  const int R = J.R1 + J.R2;
+  const int cols = J.cols;
+  const bool vec = (cols % E) == 0;
+  const int nv = cols / E;
+  for (int r = gw; r < R; r += tw) {
+    const T* row = r < J.R1 ? J.M1 + (size_t)r * cols : J.M2 + (size_t)(r - J.R1) * cols;
+    double tot;
+    if (ACC) {
+      typename AccurateAcc<T>::type a;
+      if (vec) {
+        const V* rv = (const V*)row;
+        const V* vv = (const V*)v;
+        for (int c = lane; c < nv; c += 32) {
+          const V m = ldg_stream<T>(rv + c);
+          const V x = vv[c];
+          if constexpr (E == 4) {
+            a.add(m.x, x.x); a.add(m.y, x.y); a.add(m.z, x.z); a.add(m.w, x.w);
+          } else {
+            a.add(m.x, x.x); a.add(m.y, x.y);
+          }
+        }
+      } else {
+        for (int c = lane; c < cols; c += 32) a.add(row[c], v[c]);
+      }
+      tot = a.get();
+    } else {
+      T s = T(0), comp = T(0);  // Kahan pair over short FMA chains
+      auto kadd = [&](T t) {
+        const T yk = t - comp;
+        const T tk = s + yk;
+        comp = (tk - s) - yk;
+        s = tk;
+      };
+      if (vec) {
+        const V* rv = (const V*)row;
+        const V* vv = (const V*)v;
+        int c = lane;
+        for (; c + 96 < nv; c += 128) {
+          const V m0 = ldg_stream<T>(rv + c), m1 = ldg_stream<T>(rv + c + 32);
+          const V m2 = ldg_stream<T>(rv + c + 64), m3 = ldg_stream<T>(rv + c + 96);
+          const T d0 = vdot(m0, vv[c]), d1 = vdot(m1, vv[c + 32]);
+          const T d2 = vdot(m2, vv[c + 64]), d3 = vdot(m3, vv[c + 96]);
+          kadd((d0 + d1) + (d2 + d3));
+        }
+        for (; c < nv; c += 32) kadd(vdot(ldg_stream<T>(rv + c), vv[c]));
+      } else {
+        for (int c = lane; c < cols; c += 32) kadd(row[c] * v[c]);
+      }
+      tot = double(s) - double(comp);
+    }
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
+    if (lane == 0) {
+      if (r < J.R1) {
+        if (J.add1) tot += double(J.add1[r]);
+        if (ACC) J.dout1[r] = tot; else J.out1[r] = T(tot);
+      } else {
+        if (ACC) J.dout2[r - J.R1] = tot; else J.out2[r - J.R1] = T(tot);
+      }
+    }
+  }
+}
+
+// Deterministic grid reduction: every block writes its partial sums, the last
+// block to arrive adds them in block order.
+template <int NQ>
+__device__ __forceinline__ bool grid_reduce(double (&part)[NQ], double* partials, Ctrl* ctrl,
+                                            double* out) {
+  __shared__ double red[NQ][33];
+  __shared__ bool last;
+  for (int q = 0; q < NQ; ++q) {
+    double v = part[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += red[q][w];
+      partials[blockIdx.x * NQ + q] = s;
+    }
+    __threadfence();
+    const unsigned int t = atomicAdd(&ctrl->arrive, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    for (int q = 0; q < NQ; ++q) {
+      double s = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double*)partials)[b * NQ + q];
+      out[q] = s;
+    }
+    ctrl->arrive = 0;
+  }
+  __syncthreads();
+  return true;
+}
+
+// Inner stopping certificate at x (eq. duquad_in): gradient Qx + add + add2,
+// gradient-mapping bound (sigma > 0) or Frank-Wolfe gap.  Sets the done flag.
+template <typename T>
+__global__ void __launch_bounds__(512) k_cert(const T* x, const T* Qx, const T* add, const T* add2,
+                                              const T* lb, const T* ub, int n, double L, double sigma,
+                                              double eps_in, int k, int max_inner, double* partials,
+                                              Ctrl* ctrl) {
+  if (*(volatile int*)&ctrl->inner_done) return;
+  const double kap = sigma > 0.0 ? 1.0 / (2.0 * sigma) - 1.0 / (2.0 * L) : 0.0;
+  double part[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const T gr = Qx[i] + add[i] + (add2 ? add2[i] : T(0));
+    const double gd = double(gr), xd = double(x[i]);
+    if (sigma > 0.0) {
+      const double xp = fmin(fmax(xd - gd / L, double(lb[i])), double(ub[i]));
+      const double d = xd - xp;
+      part[0] += gd * d + (L * d) * (L * d) * kap;
+    } else {
+      const double a = gd * double(lb[i]), b = gd * double(ub[i]);
+      part[0] += gd * xd - (a < b ? a : b);
+    }
+  }
+  double out[1];
+  if (grid_reduce<1>(part, partials, ctrl, out) && threadIdx.x == 0) {
+    ctrl->cert = out[0];
+    if (out[0] <= eps_in || k >= max_inner) {
+      ctrl->inner_done = 1;
+      ctrl->k_stop = k;
+    }
+  }
+}
+
+// Dual step of Algorithm DFOM and the running average of eq. average_primal.
+template <typename T>
+__global__ void k_dual(const T* Gx, const T* g, const T* mu, T* lam, int p, T alpha, T rho, int cone,
+                       int kd_plus, const T* x, double* usum, double theta, int n) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int j = tid; j < p; j += nt) {
+    const T r = Gx[j] + g[j];
+    const T s = rho > T(0) ? proj_K(cone, r + mu[j] / rho) : T(0);
+    lam[j] = proj_Kd(cone, kd_plus != 0, mu[j] + alpha * (r - s));
+  }
+  for (int i = tid; i < n; i += nt) usum[i] += theta * double(x[i]);
+}
+
+template <typename T>
+__global__ void k_momentum(const T* lam, T* lamp, T* mu, int p, T beta) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x) {
+    const T l = lam[j];
+    mu[j] = l + beta * (l - lamp[j]);
+    lamp[j] = l;
+  }
+}
+
+template <typename T>
+__global__ void k_init(T* x, const T* x0, const T* lb, const T* ub, int n, T* lam, T* lamp, T* mu,
+                       const T* lam0, int p, double* usum) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int i = tid; i < n; i += nt) {
+    x[i] = x0 ? x0[i] : clampT(T(0), lb[i], ub[i]);
+    usum[i] = 0.0;
+  }
+  for (int j = tid; j < p; j += nt) {
+    const T l = lam0 ? lam0[j] : T(0);
+    lam[j] = l; lamp[j] = l; mu[j] = l;
+  }
+}
+
+template <typename T>
+__global__ void k_avg(const double* usum, double S, T* out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    out[i] = T(usum[i] / S);
+}
+
+// Evaluation, part 1: F(u), dist_K(Gu+g)^2 and the Lagrangian terms from the
+// FP64 products dQ = Q u, dG = G u; forms w(u) split into a T pair.
+template <typename T>
+__global__ void __launch_bounds__(512) k_eval1(const T* u, const double* dQ, const double* dG, const T* q,
+                                               const T* g, const T* mu, int n, int p, double rho, int cone,
+                                               T* whi, T* wlo, double* partials, Ctrl* ctrl) {
+  double part[3] = {0.0, 0.0, 0.0};
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (int i = tid; i < n; i += nt) part[0] += 0.5 * double(u[i]) * dQ[i] + double(q[i]) * double(u[i]);
+  for (int j = tid; j < p; j += nt) {
+    const double r = dG[j] + double(g[j]);
+    const double d = r - proj_K(cone, r);
+    part[1] += d * d;
+    if (mu) {
+      const double mj = double(mu[j]);
+      double w;
+      if (rho > 0.0) {
+        const double z = r + mj / rho;
+        const double dz = z - proj_K(cone, z);
+        part[2] += 0.5 * rho * dz * dz - mj * mj / (2.0 * rho);
+        w = rho * dz;
+      } else {
+        part[2] += mj * r;
+        w = mj;
+      }
+      const T hi = T(w);
+      whi[j] = hi;
+      wlo[j] = T(w - double(hi));
+    }
+  }
+  double out[3];
+  if (grid_reduce<3>(part, partials, ctrl, out) && threadIdx.x == 0) {
+    ctrl->sums[0] = out[0];
+    ctrl->sums[1] = out[1];
+    ctrl->sums[2] = out[2];
+  }
+}
+
+// Evaluation, part 2: certificate at u from grad = dQ + q + (G' w_hi + G' w_lo).
+template <typename T>
+__global__ void __launch_bounds__(512) k_eval2(const T* u, const double* dQ, const T* q, const double* gw_hi,
+                                               const double* gw_lo, const T* lb, const T* ub, int n, double L,
+                                               double sigma, double* partials, Ctrl* ctrl) {
+  const double kap = sigma > 0.0 ? 1.0 / (2.0 * sigma) - 1.0 / (2.0 * L) : 0.0;
+  double part[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double gd = dQ[i] + double(q[i]) + (gw_hi ? gw_hi[i] + gw_lo[i] : 0.0);
+    const double xd = double(u[i]);
+    if (sigma > 0.0) {
+      const double xp = fmin(fmax(xd - gd / L, double(lb[i])), double(ub[i]));
+      const double d = xd - xp;
+      part[0] += gd * d + (L * d) * (L * d) * kap;
+    } else {
+      const double a = gd * double(lb[i]), b = gd * double(ub[i]);
+      part[0] += gd * xd - (a < b ? a : b);
+    }
+  }
+  double out[1];
+  if (grid_reduce<1>(part, partials, ctrl, out) && threadIdx.x == 0) ctrl->sums[3] = out[0];
+}
+
+// Power-iteration helpers: sums v.w and w.w; then v = w / ||w||.
+template <typename T>
+__global__ void __launch_bounds__(512) k_vw(const T* v, const T* w, int n, double* partials, Ctrl* ctrl) {
+  double part[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    part[0] += double(v[i]) * double(w[i]);
+    part[1] += double(w[i]) * double(w[i]);
+  }
+  double out[2];
+  if (grid_reduce<2>(part, partials, ctrl, out) && threadIdx.x == 0) {
+    ctrl->sums[4] = out[0];
+    ctrl->sums[5] = out[1];
+  }
+}
+
+template <typename T>
+__global__ void k_scale(const T* w, T* v, int n, const Ctrl* ctrl, T fill) {
+  const double ww = ctrl->sums[5];
+  const double inv = ww > 0.0 ? 1.0 / sqrt(ww) : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    v[i] = fill != T(0) ? fill : T(double(w[i]) * inv);
+}
+
+template <typename T>
+__global__ void k_add(T* a, const T* b, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] += b[i];
+}
+
+// ---------------------------------------------------------------- host side
+
+struct GridWs {
+  int prec = 0;
+  size_t esz = 4;
+  void* mem = nullptr;
+  Ctrl* ctrl = nullptr;
+  Ctrl* hctrl = nullptr;    // pinned mirror
+  double* partials = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> evpool;  // GEMV timing events (profiling)
+  // vectors (element pointers into mem)
+  void *X[3], *QX[3], *GX[3], *XB[3], *QXB[3], *GXB[3];
+  void *c, *tn, *w, *whi, *wlo, *mu, *lam, *lamp, *ul, *uavg, *pv, *pw, *pt;
+  double *usum, *dQ, *dG, *gwh, *gwl;
+  int blocks = 0;
+};
+
+void grid_free(GridWs* w) {
+  if (!w) return;
+  if (w->mem) cudaFree(w->mem);
+  if (w->ctrl) cudaFree(w->ctrl);
+  if (w->hctrl) cudaFreeHost(w->hctrl);
+  if (w->partials) cudaFree(w->partials);
+  for (auto& e : w->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : w->evpool) cudaEventDestroy(e);
+  delete w;
+}
+
+static dq_status grid_ws(dq_problem* P, GridWs** out) {
+  if (P->gws) {
+    *out = P->gws;
+    return DQ_OK;
+  }
+  GridWs* W = new GridWs();
+  W->prec = P->prec;
+  W->esz = P->esz;
+  const size_t n = P->n, pn = std::max(P->p, 1);
+  auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t vn = a256(n * W->esz), vp = a256(pn * W->esz), dn = a256(n * 8), dp = a256(pn * 8);
+  const size_t total = 12 * vn + 6 * vp + 3 * vn /*c tn ul*/ + 2 * vn /*uavg pv*/ + vn /*pw*/ + vp /*pt*/ +
+                       6 * vp /*w whi wlo mu lam lamp*/ + 4 * dn /*usum dQ gwh gwl*/ + dp /*dG*/;
+  if (cudaMalloc(&W->mem, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete W;
+    set_error("grid workspace allocation (%zu bytes) failed", total);
+    return DQ_ERR_NOMEM;
+  }
+  char* b = (char*)W->mem;
+  auto take = [&](size_t bytes) {
+    void* r = b;
+    b += bytes;
+    return r;
+  };
+  for (int i = 0; i < 3; ++i) {
+    W->X[i] = take(vn); W->QX[i] = take(vn); W->XB[i] = take(vn); W->QXB[i] = take(vn);
+  }
+  for (int i = 0; i < 3; ++i) { W->GX[i] = take(vp); W->GXB[i] = take(vp); }
+  W->c = take(vn); W->tn = take(vn); W->ul = take(vn); W->uavg = take(vn); W->pv = take(vn); W->pw = take(vn);
+  W->pt = take(vp);
+  W->w = take(vp); W->whi = take(vp); W->wlo = take(vp); W->mu = take(vp); W->lam = take(vp); W->lamp = take(vp);
+  W->usum = (double*)take(dn); W->dQ = (double*)take(dn); W->gwh = (double*)take(dn); W->gwl = (double*)take(dn);
+  W->dG = (double*)take(dp);
+  W->blocks = P->ctx->num_sms * 2;
+  if (cudaMalloc(&W->ctrl, sizeof(Ctrl)) != cudaSuccess || cudaMallocHost(&W->hctrl, 2 * sizeof(Ctrl)) != cudaSuccess ||
+      cudaMalloc(&W->partials, sizeof(double) * 8 * 4096) != cudaSuccess ||
+      cudaEventCreateWithFlags(&W->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&W->ev[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    grid_free(W);
+    set_error("grid control allocation failed");
+    return DQ_ERR_NOMEM;
+  }
+  cudaMemsetAsync(W->ctrl, 0, sizeof(Ctrl), P->ctx->stream);
+  P->gws = W;
+  *out = W;
+  return DQ_OK;
+}
+
+template <typename T>
+struct GridRun {
+  dq_problem* P;
+  GridWs* W;
+  cudaStream_t st;
+  int n, p, cone, blocks;
+  double LL, sigma, Ld, rho, eps_in;
+  int kd_plus;
+  const SolveCfg* cfg;
+  long long inner_total = 0;
+  const T* Q() const { return (const T*)P->Q; }
+  const T* G() const { return (const T*)P->G; }
+  const T* GT() const { return (const T*)P->GT; }
+  const T* q() const { return (const T*)P->q; }
+  const T* g() const { return (const T*)P->g; }
+  const T* lb() const { return (const T*)P->lb; }
+  const T* ub() const { return (const T*)P->ub; }
+  T* v(void* a) const { return (T*)a; }
+
+  template <bool ACC>
+  cudaError_t rows(RowJob<T> J) {
+    size_t smem = (size_t)J.cols * sizeof(T);
+    auto kern = k_rows<T, ACC>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, 512, smem, st>>>(J);
+    ++P->ctx->launches;
+    return cudaGetLastError();
+  }
+  RowJob<T> job() const {
+    RowJob<T> J;
+    memset(&J, 0, sizeof(J));
+    J.cone = cone;
+    return J;
+  }
+  // out1 = M1 v (+add1), out2 = M2 v with v a plain vector
+  cudaError_t gemv(const T* M1, int R1, const T* M2, int R2, int cols, const T* vin, T* o1, T* o2,
+                   const T* add1 = nullptr) {
+    RowJob<T> J = job();
+    J.M1 = M1; J.R1 = R1; J.M2 = M2; J.R2 = R2; J.cols = cols; J.out1 = o1; J.out2 = o2; J.add1 = add1;
+    J.vmode = VM_COPY; J.a0 = vin;
+    return rows<false>(J);
+  }
+  cudaError_t gemv_acc(const T* M1, int R1, const T* M2, int R2, int cols, const T* vin, double* o1,
+                       double* o2) {
+    RowJob<T> J = job();
+    J.M1 = M1; J.R1 = R1; J.M2 = M2; J.R2 = R2; J.cols = cols; J.dout1 = o1; J.dout2 = o2;
+    J.vmode = VM_COPY; J.a0 = vin;
+    return rows<true>(J);
+  }
+
+  // lambda_max of Q (which = 0) or G'G (which = 1) by power iteration.
+  dq_status power(int which, double* out) {
+    T* vv = v(W->pv);
+    T* ww = v(W->pw);
+    T* tt = v(W->pt);
+    const int eb = std::min(blocks, 4096);
+    k_scale<T><<<eb, 256, 0, st>>>(ww, vv, n, W->ctrl, T(1.0 / sqrt(double(n))));
+    double theta = 0.0, r = 0.0;
+    for (int it = 0; it < 300; ++it) {
+      cudaError_t e;
+      if (which == 0) {
+        e = gemv(Q(), n, nullptr, 0, n, vv, ww, nullptr);
+      } else {
+        e = gemv(G(), p, nullptr, 0, n, vv, tt, nullptr);
+        if (e == cudaSuccess) e = gemv(GT(), n, nullptr, 0, p, tt, ww, nullptr);
+      }
+      if (e != cudaSuccess) {
+        set_error("power iteration launch: %s", cudaGetErrorString(e));
+        return DQ_ERR_CUDA;
+      }
+      k_vw<T><<<eb, 512, 0, st>>>(vv, ww, n, W->partials, W->ctrl);
+      P->ctx->launches += 2;  // k_vw and the k_scale before it
+      DQ_CK(cudaMemcpyAsync(W->hctrl, W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      DQ_CK(cudaStreamSynchronize(st));
+      const double vw = W->hctrl->sums[4], ww2 = W->hctrl->sums[5];
+      theta = vw;
+      r = sqrt(std::max(ww2 - vw * vw, 0.0));
+      if (ww2 == 0.0 || (it >= 3 && r <= 1e-3 * theta)) break;
+      k_scale<T><<<eb, 256, 0, st>>>(ww, vv, n, W->ctrl, T(0));
+    }
+    *out = theta + r;
+    return DQ_OK;
+  }
+
+  // Copy (x, Qx, Gx) from slot `from` of chain S to slots 0 and 2 of chain D.
+  cudaError_t seed_chain(void* const* Sx, void* const* SQ, void* const* SG, int from, void* const* Dx,
+                         void* const* DQ_, void* const* DG) {
+    const size_t bn = (size_t)n * sizeof(T), bp = (size_t)std::max(p, 1) * sizeof(T);
+    for (int d : {0, 2}) {
+      if (!(Dx == Sx && d == from)) {
+        cudaMemcpyAsync(Dx[d], Sx[from], bn, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(DQ_[d], SQ[from], bn, cudaMemcpyDeviceToDevice, st);
+        if (p) cudaMemcpyAsync(DG[d], SG[from], bp, cudaMemcpyDeviceToDevice, st);
+      }
+    }
+    return cudaGetLastError();
+  }
+
+  // Algorithm FOM on L_rho(., mu) over the box for the chain (X, QX, GX)
+  // whose current iterate is in slot 0 (and slot 2).  Returns the slot of ubar.
+  dq_status fom(void* const* X, void* const* QX, void* const* GX, const T* mu, int* slot) {
+    const bool aug = rho > 0.0;
+    cudaError_t e = cudaSuccess;
+    if (!aug) {  // c = q + G' mu (rows of G')
+      if (p > 0) e = gemv(GT(), n, nullptr, 0, p, mu, v(W->c), nullptr, q());
+      else e = cudaMemcpyAsync(W->c, q(), (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) { set_error("fom setup: %s", cudaGetErrorString(e)); return DQ_ERR_CUDA; }
+    }
+    DQ_CK(cudaMemsetAsync(W->ctrl, 0, sizeof(Ctrl), st));
+    const bool fgm_sigma = sigma > 0.0;
+    const double beta_sigma = (sqrt(LL) - sqrt(sigma)) / (sqrt(LL) + sqrt(sigma));
+    double theta = 1.0, beta = 0.0;
+    const int fixed = cfg->fixed_inner;
+    const int m = cfg->inner_check_every;
+    const int kmax = fixed > 0 ? fixed : cfg->max_inner;
+    const int eb = std::min(blocks, 4096);
+    int k = 0, chunk = 0, kstop = -1;
+    auto slot_of = [](int kk) { return ((kk % 3) + 3) % 3; };
+    // optional CUDA-event timing of the GEMV launches (see dq_context_profile)
+    struct Rec {
+      int k, e0;
+      double bytes;
+    };
+    std::vector<Rec> recs;
+    int evn = 0;
+    auto timed = [&](const RowJob<T>& J, int kk, double bytes) -> cudaError_t {
+      if (!P->ctx->profile) return rows<false>(J);
+      while ((int)W->evpool.size() < evn + 2) {
+        cudaEvent_t ev;
+        cudaError_t ce = cudaEventCreate(&ev);
+        if (ce != cudaSuccess) return ce;
+        W->evpool.push_back(ev);
+      }
+      cudaEventRecord(W->evpool[evn], st);
+      cudaError_t ce = rows<false>(J);
+      cudaEventRecord(W->evpool[evn + 1], st);
+      recs.push_back({kk, evn, bytes});
+      evn += 2;
+      return ce;
+    };
+    while (k < kmax && kstop < 0) {
+      // one chunk of up to m iterations, then (gap mode) the certificate
+      const int kend = std::min(kmax, k + (fixed > 0 ? kmax : m));
+      for (; k < kend;) {
+        ++k;
+        const int sx = slot_of(k - 1), sxp = slot_of(k - 2), sn = slot_of(k);
+        const int* dn = fixed > 0 ? nullptr : &W->ctrl->inner_done;
+        if (aug) {  // tn = G' [mu + rho (G y + g)]_+
+          RowJob<T> J = job();
+          J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->tn);
+          J.vmode = VM_W; J.a0 = v(GX[sx]); J.a1 = v(GX[sxp]); J.a2 = mu; J.a3 = g();
+          J.beta = T(beta); J.rho = T(rho); J.done = dn;
+          const double bw = double(sizeof(T)) * (double(n) * p + 4.0 * p + n);
+          if ((e = timed(J, k, bw)) != cudaSuccess) break;
+        }
+        // x^k = [y - grad/L]_U in the prologue; then Q x^k (and G x^k)
+        RowJob<T> J = job();
+        J.M1 = Q(); J.R1 = n; J.M2 = aug ? G() : nullptr; J.R2 = aug ? p : 0; J.cols = n;
+        J.out1 = v(QX[sn]); J.out2 = aug ? v(GX[sn]) : nullptr;
+        J.vmode = VM_STEP; J.a0 = v(X[sx]); J.a1 = v(X[sxp]); J.a2 = v(QX[sx]); J.a3 = v(QX[sxp]);
+        J.a4 = aug ? q() : v(W->c); J.a5 = aug ? v(W->tn) : nullptr; J.a6 = lb(); J.a7 = ub();
+        J.beta = T(beta); J.L = T(LL); J.vout = v(X[sn]); J.done = dn;
+        const double bx = double(sizeof(T)) * (double(n) * n + (aug ? double(p) * n : 0.0) +
+                                               (aug ? 10.0 : 9.0) * n + (aug ? p : 0));
+        if ((e = timed(J, k, bx)) != cudaSuccess) break;
+        if (fgm_sigma) {
+          beta = beta_sigma;
+        } else {
+          const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+          beta = (theta - 1.0) / t1;
+          theta = t1;
+        }
+      }
+      if (e != cudaSuccess) break;
+      if (fixed > 0) break;
+      const int sc = slot_of(k);
+      if (k % m == 0 || k >= kmax) {
+        const T* add2 = nullptr;
+        if (aug) {  // gradient at x: G' [mu + rho (G x + g)]_+
+          RowJob<T> J = job();
+          J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->tn);
+          J.vmode = VM_W; J.a0 = v(GX[sc]); J.a1 = v(GX[sc]); J.a2 = mu; J.a3 = g();
+          J.beta = T(0); J.rho = T(rho); J.done = &W->ctrl->inner_done;
+          if ((e = rows<false>(J)) != cudaSuccess) break;
+          add2 = v(W->tn);
+        }
+        k_cert<T><<<eb, 512, 0, st>>>(v(X[sc]), v(QX[sc]), aug ? q() : v(W->c), add2, lb(), ub(), n, LL, sigma,
+                                       eps_in, k, kmax, W->partials, W->ctrl);
+        ++P->ctx->launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        // publish the flag; look at the previous chunk's flag (one chunk of lag)
+        cudaMemcpyAsync(&W->hctrl[chunk & 1], W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        cudaEventRecord(W->ev[chunk & 1], st);
+        if (chunk > 0) {
+          cudaEventSynchronize(W->ev[(chunk - 1) & 1]);
+          const Ctrl& hc = W->hctrl[(chunk - 1) & 1];
+          if (hc.inner_done) kstop = hc.k_stop;
+        }
+        ++chunk;
+      }
+    }
+    if (e != cudaSuccess) {
+      set_error("inner loop launch: %s", cudaGetErrorString(e));
+      return DQ_ERR_CUDA;
+    }
+    DQ_CK(cudaStreamSynchronize(st));
+    if (fixed > 0) {
+      kstop = k;
+    } else {
+      DQ_CK(cudaMemcpyAsync(W->hctrl, W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+      DQ_CK(cudaStreamSynchronize(st));
+      kstop = W->hctrl->inner_done ? W->hctrl->k_stop : k;
+    }
+    inner_total += kstop;
+    *slot = slot_of(kstop);
+    for (const Rec& r : recs) {
+      if (r.k > kstop) continue;  // returned at once: the loop had already stopped
+      float ms = 0.f;
+      DQ_CK(cudaEventElapsedTime(&ms, W->evpool[r.e0], W->evpool[r.e0 + 1]));
+      P->ctx->gemv_ms += ms;
+      P->ctx->gemv_bytes += r.bytes;
+      ++P->ctx->gemv_launches;
+    }
+    if (!aug && p > 0) {  // G ubar for the dual gradient
+      e = gemv(G(), p, nullptr, 0, n, v(X[*slot]), v(GX[*slot]), nullptr);
+      if (e != cudaSuccess) { set_error("G ubar: %s", cudaGetErrorString(e)); return DQ_ERR_CUDA; }
+    }
+    return DQ_OK;
+  }
+
+  // FP64-accurate F(u), dist_K(Gu + g) and (mu given) L_rho(u, mu), certificate.
+  dq_status eval(const T* u, const T* mu, double* F, double* infeas, double* lagr, double* cert) {
+    const int eb = std::min(blocks, 4096);
+    cudaError_t e = gemv_acc(Q(), n, G(), p, n, u, W->dQ, W->dG);
+    if (e != cudaSuccess) { set_error("eval: %s", cudaGetErrorString(e)); return DQ_ERR_CUDA; }
+    k_eval1<T><<<eb, 512, 0, st>>>(u, W->dQ, W->dG, q(), g(), mu, n, p, rho, cone, v(W->whi), v(W->wlo),
+                                   W->partials, W->ctrl);
+    if (mu) {
+      if (p > 0) {
+        if ((e = gemv_acc(GT(), n, nullptr, 0, p, v(W->whi), W->gwh, nullptr)) != cudaSuccess ||
+            (e = gemv_acc(GT(), n, nullptr, 0, p, v(W->wlo), W->gwl, nullptr)) != cudaSuccess) {
+          set_error("eval: %s", cudaGetErrorString(e));
+          return DQ_ERR_CUDA;
+        }
+      }
+      k_eval2<T><<<eb, 512, 0, st>>>(u, W->dQ, q(), p > 0 ? W->gwh : nullptr, W->gwl, lb(), ub(), n, LL, sigma,
+                                     W->partials, W->ctrl);
+    }
+    P->ctx->launches += mu ? 2 : 1;
+    DQ_CK(cudaGetLastError());
+    DQ_CK(cudaMemcpyAsync(W->hctrl, W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    DQ_CK(cudaStreamSynchronize(st));
+    *F = W->hctrl->sums[0];
+    *infeas = sqrt(W->hctrl->sums[1]);
+    if (lagr) *lagr = W->hctrl->sums[0] + W->hctrl->sums[2];
+    if (cert) *cert = W->hctrl->sums[3];
+    return DQ_OK;
+  }
+
+  bool mu_nonneg(const T* m) {
+    if (rho > 0.0 || cone == CONE_EQ || p == 0) return true;
+    std::vector<T> h(p);
+    if (cudaMemcpy(h.data(), m, (size_t)p * sizeof(T), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    for (int j = 0; j < p; ++j)
+      if (h[j] < T(0)) return false;
+    return true;
+  }
+
+  dq_status solve(const dq_outputs* out, dq_result* res) {
+    const int eb = std::min(blocks, 4096);
+    const bool warm = cfg->warm_start && P->has_state;
+    const bool fast = alg_fast(cfg->alg);
+    k_init<T><<<eb, 256, 0, st>>>(v(W->X[0]), warm ? (const T*)P->x_state : nullptr, lb(), ub(), n, v(W->lam),
+                                  v(W->lamp), v(W->mu), warm ? (const T*)P->lam_state : nullptr, p, W->usum);
+    DQ_CK(cudaGetLastError());
+    cudaError_t e = gemv(Q(), n, p > 0 ? G() : nullptr, p, n, v(W->X[0]), v(W->QX[0]), p > 0 ? v(W->GX[0]) : nullptr);
+    if (e != cudaSuccess) { set_error("init: %s", cudaGetErrorString(e)); return DQ_ERR_CUDA; }
+    int cur = 0;
+    double theta = 1.0, S = 0.0, d_lb = -INFINITY;
+    double f_last = NAN, i_last = NAN, f_avg = NAN, i_avg = NAN;
+    int conv_last = 0, conv_avg = 0, status = ST_OK, k = 0;
+    bool done = false, last_from_B = false;
+    int slotB = 0;
+    const int kmax = cfg->fixed_outer > 0 ? cfg->fixed_outer : cfg->max_outer;
+    const bool want_last = (cfg->output & DQ_OUT_LAST) != 0, want_avg = (cfg->output & DQ_OUT_AVERAGE) != 0;
+    while (k < kmax && !done) {
+      ++k;
+      dq_status s;
+      if ((e = seed_chain(W->X, W->QX, W->GX, cur, W->X, W->QX, W->GX)) != cudaSuccess) break;
+      if ((s = fom(W->X, W->QX, W->GX, v(W->mu), &cur)) != DQ_OK) return s;
+      k_dual<T><<<eb, 256, 0, st>>>(v(W->GX[cur]), g(), v(W->mu), v(W->lam), p, T(1.0 / (2.0 * Ld)), T(rho), cone,
+                                    kd_plus, v(W->X[cur]), W->usum, theta, n);
+      S += theta;
+      double beta = 0.0;
+      if (fast) {
+        const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+        beta = (theta - 1.0) / t1;
+        theta = t1;
+      }
+      const bool final_iter = (k == kmax);
+      if (final_iter || (cfg->fixed_outer <= 0 && k % cfg->check_every == 0)) {
+        double F, inf, lag, cert;
+        if (mu_nonneg(v(W->mu))) {
+          if ((s = eval(v(W->X[cur]), v(W->mu), &F, &inf, &lag, &cert)) != DQ_OK) return s;
+          d_lb = std::max(d_lb, lag - cert);
+        }
+        if (want_last) {
+          if (fast) {
+            if ((e = seed_chain(W->X, W->QX, W->GX, cur, W->XB, W->QXB, W->GXB)) != cudaSuccess) break;
+            if ((s = fom(W->XB, W->QXB, W->GXB, v(W->lam), &slotB)) != DQ_OK) return s;
+            last_from_B = true;
+            const bool ok = mu_nonneg(v(W->lam));
+            if ((s = eval(v(W->XB[slotB]), ok ? v(W->lam) : nullptr, &F, &inf, &lag, &cert)) != DQ_OK) return s;
+            if (ok) d_lb = std::max(d_lb, lag - cert);
+          } else {
+            last_from_B = false;
+            if ((s = eval(v(W->X[cur]), nullptr, &F, &inf, nullptr, nullptr)) != DQ_OK) return s;
+          }
+          f_last = F;
+          i_last = inf;
+        }
+        if (want_avg) {
+          k_avg<T><<<eb, 256, 0, st>>>(W->usum, S, v(W->uavg), n);
+          if ((s = eval(v(W->uavg), nullptr, &F, &inf, nullptr, nullptr)) != DQ_OK) return s;
+          f_avg = F;
+          i_avg = inf;
+        }
+        if ((want_last && !(std::isfinite(f_last) && std::isfinite(i_last))) ||
+            (want_avg && !(std::isfinite(f_avg) && std::isfinite(i_avg)))) {
+          status = ST_NONFINITE;
+          done = true;
+        }
+        if (cfg->fixed_outer <= 0 && !done) {
+          conv_last = want_last && i_last <= cfg->eps_out && f_last - d_lb <= cfg->eps_out;
+          conv_avg = want_avg && i_avg <= cfg->eps_out && f_avg - d_lb <= cfg->eps_out;
+          done = conv_last || conv_avg;
+        }
+      }
+      k_momentum<T><<<eb, 256, 0, st>>>(v(W->lam), v(W->lamp), v(W->mu), p, T(beta));
+      P->ctx->launches += (want_avg && (final_iter || (cfg->fixed_outer <= 0 && k % cfg->check_every == 0))) ? 3 : 2;
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+    }
+    if (e != cudaSuccess) {
+      set_error("outer loop: %s", cudaGetErrorString(e));
+      return DQ_ERR_CUDA;
+    }
+    k_avg<T><<<eb, 256, 0, st>>>(W->usum, S, v(W->uavg), n);
+    P->ctx->launches += 2;  // k_init and this k_avg
+    const size_t bn = (size_t)n * sizeof(T), bp = (size_t)p * sizeof(T);
+    const void* xl = (want_last && last_from_B) ? W->XB[slotB] : W->X[cur];
+    DQ_CK(cudaMemcpyAsync(P->x_state, W->X[cur], bn, cudaMemcpyDeviceToDevice, st));
+    if (p) DQ_CK(cudaMemcpyAsync(P->lam_state, W->lam, bp, cudaMemcpyDeviceToDevice, st));
+    P->has_state = true;
+    if (out) {
+      const cudaMemcpyKind kd = out->memory == DQ_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+      std::vector<T> h;
+      auto put = [&](void* dst, const void* src, size_t cnt) -> dq_status {
+        if (!dst || cnt == 0) return DQ_OK;
+        if (out->memory == DQ_DEVICE) {
+          DQ_CK(cudaMemcpyAsync(dst, src, cnt * sizeof(T), kd, st));
+        } else {
+          h.resize(cnt);
+          DQ_CK(cudaMemcpyAsync(h.data(), src, cnt * sizeof(T), kd, st));
+          DQ_CK(cudaStreamSynchronize(st));
+          for (size_t i = 0; i < cnt; ++i) ((double*)dst)[i] = double(h[i]);
+        }
+        return DQ_OK;
+      };
+      dq_status s;
+      if ((s = put(out->x_last, xl, n)) != DQ_OK) return s;
+      if ((s = put(out->x_avg, W->uavg, n)) != DQ_OK) return s;
+      if ((s = put(out->lambda, W->lam, p)) != DQ_OK) return s;
+    }
+    DQ_CK(cudaStreamSynchronize(st));
+    DevResult d;
+    d.status = status != ST_OK ? status : ((cfg->fixed_outer > 0 || conv_last || conv_avg) ? ST_OK : ST_NOT_CONVERGED);
+    d.outer_iters = k;
+    d.inner_iters = inner_total;
+    d.converged_last = conv_last;
+    d.converged_avg = conv_avg;
+    d.f_last = f_last; d.infeas_last = i_last; d.f_avg = f_avg; d.infeas_avg = i_avg; d.d_lb = d_lb;
+    const double consts[6] = {P->lmax_Q, P->normG2, LL, Ld, sigma, rho};
+    fill_result(res, d, consts, *cfg);
+    return (dq_status)d.status;
+  }
+};
+
+template <typename T>
+static dq_status constants_T(dq_problem* P, GridWs* W) {
+  GridRun<T> R;
+  R.P = P; R.W = W; R.st = P->ctx->stream; R.n = P->n; R.p = P->p; R.cone = P->cone; R.blocks = W->blocks;
+  R.cfg = nullptr;
+  dq_status s;
+  if (isnan(P->lmax_Q) && (s = R.power(0, &P->lmax_Q)) != DQ_OK) return s;
+  if (isnan(P->normG2)) {
+    if (P->p == 0) P->normG2 = 0.0;
+    else if ((s = R.power(1, &P->normG2)) != DQ_OK) return s;
+  }
+  return DQ_OK;
+}
+
+dq_status grid_constants(dq_problem* P) {
+  GridWs* W;
+  dq_status s = grid_ws(P, &W);
+  if (s != DQ_OK) return s;
+  return P->prec == DQ_FP64 ? constants_T<double>(P, W) : constants_T<float>(P, W);
+}
+
+template <typename T>
+static dq_status solve_T(dq_problem* P, GridWs* W, const SolveCfg& c, const dq_outputs* out, dq_result* res) {
+  GridRun<T> R;
+  R.P = P; R.W = W; R.st = P->ctx->stream; R.n = P->n; R.p = P->p; R.cone = P->cone; R.blocks = W->blocks;
+  R.cfg = &c;
+  const double lmin = isnan(P->lmin_Q) ? 0.0 : P->lmin_Q;
+  R.rho = isnan(c.rho) ? ((c.alg == DQ_ADGM || c.alg == DQ_ADFGM) ? (P->normG2 > 0 ? 1.0 / P->normG2 : 1.0) : 0.0) : c.rho;
+  R.LL = isnan(c.LL) ? P->lmax_Q + R.rho * P->normG2 : c.LL;
+  R.sigma = isnan(c.sigma) ? lmin : c.sigma;
+  if (isnan(c.Ld)) {
+    const double den = lmin + R.rho * P->normG2;
+    R.Ld = P->normG2 > 0 ? (den > 0 ? P->normG2 / den : INFINITY) : 1.0;
+  } else {
+    R.Ld = c.Ld;
+  }
+  if (!(R.Ld < INFINITY) || !(R.LL > 0)) {
+    set_error("DGM/DFGM need lmin_Q > 0 (Case 1)");
+    return DQ_ERR_INVALID;
+  }
+  R.eps_in = isnan(c.eps_in) ? ((c.alg == DQ_DGM || c.alg == DQ_ADGM) ? c.eps_out / 4.0
+                                                                     : c.eps_out * sqrt(c.eps_out) / (8.0 * sqrt(2.0 * R.Ld)))
+                             : c.eps_in;
+  R.kd_plus = !(c.kd_literal && !(lmin > 0.0));
+  return R.solve(out, res);
+}
+
+dq_status grid_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_result* res) {
+  std::lock_guard<std::mutex> lk(P->mu);
+  GridWs* W;
+  dq_status s = grid_ws(P, &W);
+  if (s != DQ_OK) return s;
+  if (isnan(P->lmax_Q) || isnan(P->normG2)) {
+    s = P->prec == DQ_FP64 ? constants_T<double>(P, W) : constants_T<float>(P, W);
+    if (s != DQ_OK) return s;
+  }
+  return P->prec == DQ_FP64 ? solve_T<double>(P, W, c, out, res) : solve_T<float>(P, W, c, out, res);
+}
+
+}  // namespace dq

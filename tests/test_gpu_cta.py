@@ -1,0 +1,182 @@
+"""GPU parity of the whole-solve-per-CTA engine against the FP64 oracle, through the C ABI.
+
+FP64: ||x - x_oracle|| / ||x_oracle|| <= 1e-9 at equal iteration counts with the
+same constants on both sides.  FP32: the FP64 re-scoring by the oracle is
+eps-optimal and ||x - x_oracle|| / ||x_oracle|| <= 1e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import ALG_IDS, exact_constants, gpu_opts_from, gpu_problem, oracle_qp, rel
+
+pytestmark = pytest.mark.gpu
+ALGS = ("DGM", "DFGM", "ADGM", "ADFGM")
+TOL64 = 1e-9
+TOL32 = 1e-3
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1504_05708_gb300 import duquad as D
+    c = D.Context(0)
+    yield c
+    c.close()
+
+
+def _c0(g_scale):
+    return W.single_dense(n=50, p=25, seed=0, g_scale=g_scale)
+
+
+@pytest.mark.parametrize("g_scale", [1.0, 0.02])
+@pytest.mark.parametrize("alg", ALGS)
+def test_fp64_fixed_counts_parity(ctx, alg, g_scale):
+    """The n=50, p=25 FP64 case (and an active-set variant) at equal iteration counts."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = _c0(g_scale)
+    c = exact_constants(inst, alg)
+    ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, inner_fixed=15, outer_fixed=12)
+    P = gpu_problem(ctx, inst, D.FP64)
+    xl, xa, lam, (r,) = P.solve(gpu_opts_from(c, alg, inner_stop=D.INNER_FIXED, fixed_inner=15,
+                                                fixed_outer=12, engine=D.ENGINE_CTA))
+    assert r.status == 0 and r.outer_iters == 12 and r.inner_iters == ro.inner_iters
+    assert rel(xl, ro.x_last) <= TOL64
+    assert rel(xa, ro.x_avg) <= TOL64
+    if inst.p:
+        assert rel(lam, ro.lam) <= TOL64 or np.linalg.norm(ro.lam) == 0 and np.all(lam == 0)
+    assert abs(r.f_last - ro.f_last) <= 1e-9 * max(1, abs(ro.f_last))
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_fp64_certificate_mode_parity(ctx, alg):
+    """Certificate stopping (inner and outer): same iteration counts and the same iterate."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = _c0(0.02)
+    c = exact_constants(inst, alg)
+    eps_in = O.default_eps_in(ALG_IDS[alg], 1e-4, c.Ld)
+    ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, eps_in=eps_in, eps_out=1e-4, max_outer=20000)
+    P = gpu_problem(ctx, inst, D.FP64)
+    xl, xa, lam, (r,) = P.solve(gpu_opts_from(c, alg, eps_in=eps_in, eps_out=1e-4, max_outer=20000,
+                                                engine=D.ENGINE_CTA))
+    assert r.status == ro.status == 0
+    assert (r.outer_iters, r.inner_iters) == (ro.outer_iters, ro.inner_iters)
+    assert rel(xl, ro.x_last) <= TOL64 and rel(xa, ro.x_avg) <= TOL64
+    assert abs(r.d_lb - ro.d_lb) <= 1e-9 * max(1, abs(ro.d_lb))
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_fp32_eps_optimal_and_close(ctx, alg):
+    from paper_1504_05708_gb300 import duquad as D
+    from oracle.kkt import solve_kkt
+    inst = W.single_dense(n=12, p=6, seed=31, g_scale=0.02, box=0.3, lam_lo=1.0, lam_hi=50.0)
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+    eps = 1e-3
+    P = gpu_problem(ctx, inst, D.FP32)
+    xl, xa, lam, (r,) = P.solve(D.opts(alg, eps_out=eps, engine=D.ENGINE_CTA))
+    assert r.status == 0
+    qp = oracle_qp(inst)
+    c = exact_constants(inst, alg)
+    ro = O.dfom(qp, ALG_IDS[alg], c, eps_out=eps, eps_in=O.default_eps_in(ALG_IDS[alg], eps, c.Ld))
+    for x, conv in ((xl, r.converged_last), (xa, r.converged_avg)):
+        if conv:
+            assert O.infeas(qp, x) <= eps * 1.01
+            assert O.F(qp, x) - fs <= eps
+            assert rel(x, xs) <= 5e-2  # eps-optimal points near the unique x*
+    assert rel(xl, ro.x_last) <= TOL32 or r.converged_avg
+
+
+def test_power_iteration_constants(ctx):
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=64, p=32, seed=5, lam_lo=1.0, lam_hi=1000.0)
+    P = gpu_problem(ctx, inst, D.FP32)
+    _, _, _, (r,) = P.solve(D.opts("ADFGM", fixed_outer=1, fixed_inner=1, engine=D.ENGINE_CTA))
+    lmax, lmin, nG2 = P.constants()
+    ev = np.linalg.eigvalsh(inst.Q)[-1]
+    g2 = np.linalg.norm(inst.G, 2) ** 2
+    assert ev * (1 - 1e-6) <= lmax <= ev * 1.01
+    assert g2 * (1 - 1e-6) <= nG2 <= g2 * 1.01
+    assert abs(r.rho - 1.0 / nG2) <= 1e-12 / nG2
+
+
+@pytest.mark.parametrize("n,p", [(1, 0), (1, 1), (2, 3), (3, 1), (7, 2), (33, 16), (65, 40), (257, 128)])
+def test_ragged_sizes_fp64(ctx, n, p):
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=n, p=p, seed=100 + n, g_scale=0.05, lam_lo=1.0, lam_hi=20.0)
+    for alg in ("DFGM", "ADGM"):
+        c = exact_constants(inst, alg)
+        ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, inner_fixed=7, outer_fixed=5)
+        P = gpu_problem(ctx, inst, D.FP64)
+        xl, xa, lam, (r,) = P.solve(gpu_opts_from(c, alg, fixed_inner=7, fixed_outer=5, engine=D.ENGINE_CTA))
+        assert rel(xl, ro.x_last) <= TOL64 and rel(xa, ro.x_avg) <= TOL64
+
+
+def test_box_only_closed_form(ctx):
+    from paper_1504_05708_gb300 import duquad as D
+    n = 40
+    rng = np.random.default_rng(9)
+    d = rng.uniform(0.5, 4.0, n)
+    q = rng.standard_normal(n) * 3
+    inst = W.Instance(np.diag(d), q, np.zeros((0, n)), np.zeros(0), -np.ones(n), np.ones(n), float(d.min()))
+    P = gpu_problem(ctx, inst, D.FP64)
+    xl, xa, lam, (r,) = P.solve(D.opts("DFGM", eps_out=1e-10, eps_in=1e-24, max_inner=100000,
+                                       engine=D.ENGINE_CTA))
+    np.testing.assert_allclose(xl, np.clip(-q / d, -1, 1), atol=1e-10)
+
+
+def test_batch_alone_equals_in_mix(ctx):
+    """Mixed sizes and algorithms in one persistent launch: each result is bit-identical to the
+    instance solved alone (fixed reduction order, no cross-instance state)."""
+    from paper_1504_05708_gb300 import duquad as D
+    insts = [W.uneven_instance(n, k, a, s) for n, k, a, s in
+             [(16, 10.0, 0, 1), (90, 100.0, 1, 2), (200, 1e3, 2, 3), (37, 50.0, 3, 4), (150, 20.0, 1, 5)]]
+    probs = [gpu_problem(ctx, i, D.FP32) for i in insts]
+    ops = [D.opts(i.alg, eps_out=1e-3, engine=D.ENGINE_CTA) for i in insts]
+    outs, res = D.solve_many(probs, ops)
+    for P, o, (xl, xa, lm), r in zip(probs, ops, outs, res):
+        xl1, xa1, lm1, (r1,) = P.solve(o)
+        assert np.array_equal(xl[0], xl1) and np.array_equal(xa[0], xa1)
+        assert (r.outer_iters, r.inner_iters) == (r1.outer_iters, r1.inner_iters)
+
+
+def test_device_inputs_and_outputs(ctx):
+    import torch
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=50, p=25, seed=0, g_scale=0.02)
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    P = D.Problem(ctx, t(inst.Q), t(inst.q), t(inst.G), t(inst.g), t(inst.lb), t(inst.ub), prec=D.FP64,
+                  lmin_Q=inst.lmin_Q)
+    H = gpu_problem(ctx, inst, D.FP64)
+    o = D.opts("DFGM", fixed_inner=10, fixed_outer=8, engine=D.ENGINE_CTA)
+    xl = torch.zeros(50, dtype=torch.float64, device="cuda")
+    xa = torch.zeros_like(xl)
+    lm = torch.zeros(25, dtype=torch.float64, device="cuda")
+    (r,) = P.solve(o, device_out=(xl, xa, lm))
+    torch.cuda.synchronize()
+    hl, ha, hm, (rh,) = H.solve(o)
+    assert np.array_equal(xl.cpu().numpy(), hl) and np.array_equal(lm.cpu().numpy(), hm)
+
+
+def test_invalid_inputs_rejected(ctx):
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=5, p=2, seed=1)
+    bad = W.single_dense(n=5, p=2, seed=1)
+    bad.lb[2] = 2.0
+    with pytest.raises(D.DuquadError) as e:
+        gpu_problem(ctx, bad, D.FP64)
+    assert e.value.status == D.ERR_INVALID
+    nanq = W.single_dense(n=5, p=2, seed=1)
+    nanq.q[0] = np.nan
+    with pytest.raises(D.DuquadError):
+        gpu_problem(ctx, nanq, D.FP64)
+    P = gpu_problem(ctx, inst, D.FP64)
+    with pytest.raises(D.DuquadError):
+        P.solve(D.opts("DGM", rho=0.5))
+    with pytest.raises(D.DuquadError):
+        P.solve(D.opts("DFGM", inner_stop=D.INNER_FIXED, fixed_inner=0))
+    # DGM needs lambda_min(Q) > 0 (Case 1): a zero lower bound is refused on the device
+    Z = gpu_problem(ctx, inst, D.FP64)
+    Z2 = D.Problem(ctx, inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, prec=D.FP64, lmin_Q=0.0)
+    with pytest.raises(D.DuquadError) as e:
+        Z2.solve(D.opts("DGM", engine=D.ENGINE_CTA))
+    assert e.value.status == D.ERR_INVALID

@@ -1,0 +1,105 @@
+"""GPU parity of the grid engine (one large instance over the whole GPU) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_helpers import ALG_IDS, exact_constants, gpu_opts_from, gpu_problem, oracle_qp, rel
+
+pytestmark = pytest.mark.gpu
+ALGS = ("DGM", "DFGM", "ADGM", "ADFGM")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1504_05708_gb300 import duquad as D
+    c = D.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("alg", ALGS)
+@pytest.mark.parametrize("n,p", [(301, 150), (1030, 517)])
+def test_fp64_fixed_counts_parity(ctx, alg, n, p):
+    """Sizes that span many row tiles with ragged tails (n, p not multiples of the vector width)."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=n, p=p, seed=7 + n, g_scale=0.05, lam_lo=1.0, lam_hi=30.0)
+    c = exact_constants(inst, alg)
+    ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, inner_fixed=6, outer_fixed=4)
+    P = gpu_problem(ctx, inst, D.FP64)
+    xl, xa, lam, (r,) = P.solve(gpu_opts_from(c, alg, fixed_inner=6, fixed_outer=4, engine=D.ENGINE_GRID))
+    assert r.inner_iters == ro.inner_iters
+    assert rel(xl, ro.x_last) <= 1e-9 and rel(xa, ro.x_avg) <= 1e-9
+    assert rel(lam, ro.lam) <= 1e-9 or np.linalg.norm(ro.lam) == 0
+
+
+@pytest.mark.parametrize("alg", ["DFGM", "ADFGM"])
+def test_fp64_certificate_mode_matches_counts(ctx, alg):
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=120, p=60, seed=3, g_scale=0.02, lam_lo=1.0, lam_hi=30.0)
+    c = exact_constants(inst, alg)
+    eps_in = 1e-8
+    ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, eps_in=eps_in, eps_out=1e-5, inner_check_every=3,
+                outer_check_every=2, max_outer=5000)
+    P = gpu_problem(ctx, inst, D.FP64)
+    xl, xa, lam, (r,) = P.solve(gpu_opts_from(c, alg, eps_in=eps_in, eps_out=1e-5, inner_check_every=3,
+                                                check_every=2, max_outer=5000, engine=D.ENGINE_GRID))
+    assert r.status == ro.status == 0
+    assert (r.outer_iters, r.inner_iters) == (ro.outer_iters, ro.inner_iters)
+    assert rel(xl, ro.x_last) <= 1e-9
+
+
+@pytest.mark.parametrize("alg", ["DFGM", "ADFGM"])
+def test_fp32_large_dense_eps_optimal(ctx, alg):
+    """The large dense generator at n = 1200: FP32 solve re-scored in FP64 by the oracle."""
+    from paper_1504_05708_gb300 import duquad as D
+    d = W.large_dense(n=1200, p=600, seed=1, device="cpu")
+    import torch
+    arr = {k: v.double().numpy() for k, v in d.items() if k != "lmin_Q"}
+    inst = W.Instance(arr["Q"], arr["q"], arr["G"], arr["g"], arr["lb"], arr["ub"], d["lmin_Q"])
+    eps = 1e-3
+    P = gpu_problem(ctx, inst, D.FP32)
+    xl, xa, lam, (r,) = P.solve(D.opts(alg, eps_out=eps, eps_in=1e-6, check_every=5, engine=D.ENGINE_GRID))
+    assert r.status == 0
+    qp = oracle_qp(inst)
+    c = exact_constants(inst, alg)
+    ro = O.dfom(qp, ALG_IDS[alg], c, eps_out=1e-7, eps_in=1e-10, max_outer=20000)
+    fstar_lb = ro.d_lb
+    x = xl if r.converged_last else xa
+    assert O.infeas(qp, x) <= eps * 1.01
+    assert O.F(qp, x) - fstar_lb <= eps * 1.01
+    assert rel(x, ro.x_last) <= 1e-2
+
+
+def test_full_size_sampled_step(ctx):
+    """n = 20000, p = 10000 (the large FP32 case), the launch configuration the benchmark times:
+    one outer iteration of two inner FGM_sigma steps of ADFGM from x^0 = 0, checked on sampled
+    coordinates against the oracle's FOM step written out in FP64 (eq. auglag1 gradient)."""
+    import torch
+    from paper_1504_05708_gb300 import duquad as D
+    n, p = 20000, 10000
+    d = W.large_dense(n=n, p=p, seed=1, device="cuda")
+    rho, LL, sigma, Ld = 0.3, 6.0, 0.01, 2.5
+    P = D.Problem(ctx, d["Q"], d["q"], d["G"], d["g"], d["lb"], d["ub"], prec=D.FP32, lmin_Q=0.01,
+                  lmax_Q=5.0, normG2=3.0)
+    xa = torch.zeros(n, device="cuda")
+    o = D.opts("ADFGM", rho=rho, LL=LL, sigma=sigma, Ld=Ld, fixed_inner=2, fixed_outer=1,
+               output=D.OUT_AVERAGE, engine=D.ENGINE_GRID)
+    (r,) = P.solve(o, device_out=(None, xa, None))
+    torch.cuda.synchronize()
+    x2 = xa.double().cpu().numpy()
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(n, 256, replace=False))
+    Qs = d["Q"][torch.as_tensor(idx, device="cuda")].double().cpu().numpy()
+    G = d["G"].double().cpu().numpy()
+    q, g = d["q"].double().cpu().numpy(), d["g"].double().cpu().numpy()
+    # x^1 = [0 - grad(0)/L]_U ; grad(0) = q + G' [rho g]_+ (= q since g < 0)
+    x1 = O.sampled_fom_step(q=q, g=g, G=G, Q_rows=None, rows=None, y=np.zeros(n), mu=np.zeros(p), rho=rho,
+                            L=LL, lb=-np.ones(n), ub=np.ones(n), Qy_full=np.zeros(n))
+    beta = (np.sqrt(LL) - np.sqrt(sigma)) / (np.sqrt(LL) + np.sqrt(sigma))
+    y2 = x1 + beta * x1
+    # Q y2 at the sampled rows only
+    ref = O.sampled_fom_step(q=q, g=g, G=G, Q_rows=Qs, rows=idx, y=y2, mu=np.zeros(p), rho=rho, L=LL,
+                             lb=-np.ones(n), ub=np.ones(n))
+    err = np.abs(x2[idx] - ref)
+    assert err.max() <= 2e-5, err.max()
