@@ -173,9 +173,25 @@ dq_status dq_solve(dq_problem *prob, const dq_solve_opts *opts, const dq_outputs
 
 /* Solve `count` independent problems of any sizes in one persistent launch
  * (one CTA-resident solve per instance, a device work queue, longest
- * instances first).  opts, out, results are arrays of `count` entries. */
+ * instances first), issued as a captured CUDA graph that is replayed while
+ * the inputs (handles, options, warm-start flags) stay the same.  The launch
+ * shape is the one dq_autotune chose for this size mix, else 256 threads and
+ * the device's shared-memory maximum.  opts, out are arrays of `count`
+ * entries; results holds one entry per instance (batches expand). */
 dq_status dq_solve_many(dq_problem *const *probs, int32_t count, const dq_solve_opts *opts,
                         const dq_outputs *out, dq_result *results);
+
+/* Autotune the launch shape dq_solve_many uses for this mix of problems:
+ * times short fixed-count solves (2 outer x 25 inner iterations) of up to
+ * `sample` instances spread over the mix under each candidate block size
+ * (128, 256, 512 threads) and shared-memory cap (48 KB, 112 KB, the device
+ * maximum) with CUDA events, keeps the fastest for the context under a
+ * signature of the size histogram, and persists it (file named by
+ * DQ_AUTOTUNE_CACHE, else autotune.txt next to the library).  The sampled
+ * handles' warm-start state is overwritten.  threads_out / smem_cap_out
+ * (nullable) receive the choice (smem cap 0 = device maximum). */
+dq_status dq_autotune(dq_problem *const *probs, int32_t count, const dq_solve_opts *opts, int32_t sample,
+                      int32_t *threads_out, int32_t *smem_cap_out);
 
 /* ---- serving (continuous batching) ----------------------------------------
  * dq_serve_start launches the context's persistent request loop with `slots`

@@ -253,6 +253,12 @@ dq_status dq_context_destroy(dq_context* ctx) {
   if (!ctx) return DQ_OK;
   if (ctx->serve) dq_serve_stop(ctx);
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  for (cudaEvent_t e : ctx->gev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->scratch) cudaFree(ctx->scratch);
   delete ctx;
   return DQ_OK;
@@ -467,7 +473,7 @@ dq_status dq_solve(dq_problem* P, const dq_solve_opts* o, const dq_outputs* out,
     return DQ_ERR_INVALID;
   }
   dq_problem* const probs[1] = {P};
-  return cta_solve_problems(probs, 1, &c, out, results, 0, 256);
+  return cta_solve_problems(probs, 1, &c, out, results, 0, 256, false);
 }
 
 dq_status dq_solve_many(dq_problem* const* probs, int32_t count, const dq_solve_opts* opts,
@@ -497,7 +503,13 @@ dq_status dq_solve_many(dq_problem* const* probs, int32_t count, const dq_solve_
     if (s != DQ_OK) return s;
   }
   DQ_CK(cudaSetDevice(ctx->device));
-  return cta_solve_problems(probs, count, cfgs.data(), outs, results, 0, 256);
+  int threads = 256, smem_cap = 0;
+  auto it = ctx->tuned.find(cta_signature(probs, count));
+  if (it != ctx->tuned.end()) {
+    threads = it->second.first;
+    smem_cap = it->second.second;
+  }
+  return cta_solve_problems(probs, count, cfgs.data(), outs, results, smem_cap, threads, true);
 }
 
 }  // extern "C"

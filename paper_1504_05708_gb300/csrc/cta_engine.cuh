@@ -575,8 +575,8 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
 }
 
 // Persistent kernel: CTAs pull instance indices (in `order`) from a device counter.
-template <typename T>
-__global__ void __launch_bounds__(256) cta_solve_kernel(const CtaInst<T>* __restrict__ insts,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) cta_solve_kernel(const CtaInst<T>* __restrict__ insts,
                                                         const int* __restrict__ order, int count,
                                                         int* __restrict__ next, size_t smem_bytes) {
   extern __shared__ __align__(16) unsigned char smem[];

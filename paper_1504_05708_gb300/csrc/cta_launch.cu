@@ -1,7 +1,9 @@
 // cta_launch.cu -- host side of the whole-solve-per-CTA engine: builds the
 // instance descriptors of one or many problems (shared-matrix batches expand
 // to one descriptor per instance), orders them longest-first for the device
-// work queue, sizes shared memory and launches one persistent grid.
+// work queue, sizes shared memory and launches one persistent grid.  The
+// launch (descriptor upload, queue reset, kernel, result download) can run as
+// a captured CUDA graph that is replayed while the inputs stay the same.
 #include <math.h>
 #include <string.h>
 
@@ -15,13 +17,64 @@
 namespace dq {
 
 template <typename T>
+static const void* kernel_fn(int threads) {
+  switch (threads) {
+    case 128: return (const void*)cta_solve_kernel<T, 128>;
+    case 512: return (const void*)cta_solve_kernel<T, 512>;
+    default: return (const void*)cta_solve_kernel<T, 256>;
+  }
+}
+
+template <typename T>
+static void launch(int threads, int grid, size_t smem, cudaStream_t st, const CtaInst<T>* insts, const int* order,
+                   int count, int* next) {
+  switch (threads) {
+    case 128: cta_solve_kernel<T, 128><<<grid, 128, smem, st>>>(insts, order, count, next, smem); break;
+    case 512: cta_solve_kernel<T, 512><<<grid, 512, smem, st>>>(insts, order, count, next, smem); break;
+    default: cta_solve_kernel<T, 256><<<grid, 256, smem, st>>>(insts, order, count, next, smem); break;
+  }
+}
+
+static uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = (const unsigned char*)data;
+  for (size_t i = 0; i < bytes; ++i) h = (h ^ p[i]) * 1099511628211ull;
+  return h;
+}
+
+static dq_status pinned_scratch(dq_context* ctx, size_t bytes, void** out) {
+  if (bytes > ctx->pinned_bytes) {
+    if (ctx->pinned) {
+      DQ_CK(cudaStreamSynchronize(ctx->stream));
+      if (ctx->gstream) DQ_CK(cudaStreamSynchronize(ctx->gstream));
+      cudaFreeHost(ctx->pinned);
+      ctx->pinned = nullptr;
+      ctx->pinned_bytes = 0;
+      if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+        ctx->gkey = 0;
+      }
+    }
+    const size_t b = std::max(bytes, size_t(1) << 20);
+    if (cudaMallocHost(&ctx->pinned, b) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("pinned staging allocation of %zu bytes failed", b);
+      return DQ_ERR_NOMEM;
+    }
+    ctx->pinned_bytes = b;
+  }
+  *out = ctx->pinned;
+  return DQ_OK;
+}
+
+template <typename T>
 static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, const dq_outputs* outs,
-                     dq_result* results, int smem_cap, int threads) {
+                     dq_result* results, int smem_cap, int threads, bool use_graph) {
   dq_context* ctx = probs[0]->ctx;
   cudaStream_t st = ctx->stream;
   size_t total = 0;
   for (int i = 0; i < count; ++i) total += probs[i]->batch;
-  // scratch layout: insts | order | counter | results | consts | host-output staging
+  // device scratch: insts | order | counter | results | consts | host-output staging
   size_t stage_elems = 0;
   for (int i = 0; i < count; ++i) {
     const dq_outputs* o = outs ? &outs[i] : nullptr;
@@ -35,32 +88,36 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
   const size_t b_res = a256(total * sizeof(DevResult));
   const size_t b_con = a256(total * 6 * sizeof(double));
   const size_t b_stage = a256(stage_elems * sizeof(T));
+  const size_t b_all = b_inst + b_order + b_cnt + b_res + b_con + b_stage;
   void* scratch = nullptr;
-  dq_status s = ctx_scratch(ctx, b_inst + b_order + b_cnt + b_res + b_con + b_stage, &scratch);
+  dq_status s = ctx_scratch(ctx, b_all, &scratch);
   if (s != DQ_OK) return s;
+  void* hbuf = nullptr;  // pinned mirror of the same layout
+  if ((s = pinned_scratch(ctx, b_all, &hbuf)) != DQ_OK) return s;
   char* base = (char*)scratch;
+  char* hbase = (char*)hbuf;
   CtaInst<T>* d_inst = (CtaInst<T>*)base;
   int* d_order = (int*)(base + b_inst);
   int* d_cnt = (int*)(base + b_inst + b_order);
   DevResult* d_res = (DevResult*)(base + b_inst + b_order + b_cnt);
   double* d_con = (double*)(base + b_inst + b_order + b_cnt + b_res);
   T* d_stage = (T*)(base + b_inst + b_order + b_cnt + b_res + b_con);
+  CtaInst<T>* hi = (CtaInst<T>*)hbase;
+  int* h_order = (int*)(hbase + b_inst);
+  DevResult* h_res = (DevResult*)(hbase + b_inst + b_order + b_cnt);
+  double* h_con = (double*)(hbase + b_inst + b_order + b_cnt + b_res);
+  T* h_stage = (T*)(hbase + b_inst + b_order + b_cnt + b_res + b_con);
 
-  std::vector<CtaInst<T>> hi(total);
   std::vector<double> cost(total);
   size_t vec_max = 0, want_max = 0, k = 0, so = 0;
-  struct Stage {
-    int prob;
-    size_t off;
-  };
-  std::vector<Stage> stages;
+  std::vector<size_t> stage_off(count, 0);
   for (int i = 0; i < count; ++i) {
     dq_problem* P = probs[i];
     const SolveCfg& c = cfgs[i];
     const dq_outputs* o = outs ? &outs[i] : nullptr;
     const bool host_out = o && o->memory == DQ_HOST;
     const size_t n = P->n, p = P->p, pn = std::max<size_t>(p, 1);
-    if (host_out) stages.push_back({i, so});
+    stage_off[i] = so;
     const bool warm = c.warm_start && P->has_state;
     const double lmin = P->lmin_Q;
     for (int b = 0; b < P->batch; ++b, ++k) {
@@ -123,56 +180,88 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
     return DQ_ERR_INVALID;
   }
   const size_t smem = std::max(vec_max, std::min(want_max, cap));
-  std::vector<int> order(total);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::iota(h_order, h_order + total, 0);
+  std::stable_sort(h_order, h_order + total, [&](int a, int b) { return cost[a] > cost[b]; });
 
-  auto kern = cta_solve_kernel<T>;
-  DQ_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const void* kfn = kernel_fn<T>(threads);
+  DQ_CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  DQ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
+  DQ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, smem));
   if (occ < 1) {
     set_error("CTA engine cannot be resident with %zu bytes of shared memory", smem);
     return DQ_ERR_CUDA;
   }
   const int grid = (int)std::min<size_t>(total, (size_t)ctx->num_sms * occ);
-  DQ_CK(cudaMemcpyAsync(d_inst, hi.data(), total * sizeof(CtaInst<T>), cudaMemcpyHostToDevice, st));
-  DQ_CK(cudaMemcpyAsync(d_order, order.data(), total * sizeof(int), cudaMemcpyHostToDevice, st));
-  DQ_CK(cudaMemsetAsync(d_cnt, 0, sizeof(int), st));
-  kern<<<grid, threads, smem, st>>>(d_inst, d_order, (int)total, d_cnt, smem);
+  // the whole launch as one stream-ordered sequence
+  auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+    cudaMemcpyAsync(d_inst, hi, b_inst + b_order, cudaMemcpyHostToDevice, q);
+    cudaMemsetAsync(d_cnt, 0, sizeof(int), q);
+    launch<T>(threads, grid, smem, q, d_inst, d_order, (int)total, d_cnt);
+    cudaMemcpyAsync(h_res, d_res, b_res + b_con + b_stage, cudaMemcpyDeviceToHost, q);
+    return cudaGetLastError();
+  };
   ++ctx->launches;
-  DQ_CK(cudaGetLastError());
-
-  std::vector<DevResult> hr(total);
-  std::vector<double> hc(total * 6);
-  DQ_CK(cudaMemcpyAsync(hr.data(), d_res, total * sizeof(DevResult), cudaMemcpyDeviceToHost, st));
-  DQ_CK(cudaMemcpyAsync(hc.data(), d_con, total * 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  std::vector<T> hs(stage_elems);
-  if (stage_elems)
-    DQ_CK(cudaMemcpyAsync(hs.data(), d_stage, stage_elems * sizeof(T), cudaMemcpyDeviceToHost, st));
-  DQ_CK(cudaStreamSynchronize(st));
+  if (use_graph) {
+    uint64_t key = fnv1a(hi, total * sizeof(CtaInst<T>));
+    key = fnv1a(h_order, total * sizeof(int), key);
+    const uint64_t shape[6] = {(uint64_t)total, (uint64_t)smem, (uint64_t)threads, (uint64_t)grid,
+                               (uint64_t)(uintptr_t)scratch, (uint64_t)(uintptr_t)hbuf};
+    key = fnv1a(shape, sizeof(shape), key);
+    if (!ctx->gstream) DQ_CK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+    if (!ctx->gev[0]) {
+      DQ_CK(cudaEventCreateWithFlags(&ctx->gev[0], cudaEventDisableTiming));
+      DQ_CK(cudaEventCreateWithFlags(&ctx->gev[1], cudaEventDisableTiming));
+    }
+    if (!ctx->gexec || ctx->gkey != key) {
+      if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = nullptr;
+      }
+      cudaGraph_t g;
+      DQ_CK(cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t ce = enqueue(ctx->gstream);
+      cudaError_t ce2 = cudaStreamEndCapture(ctx->gstream, &g);
+      if (ce != cudaSuccess || ce2 != cudaSuccess) {
+        set_error("graph capture failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ce2));
+        return DQ_ERR_CUDA;
+      }
+      ce = cudaGraphInstantiate(&ctx->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) {
+        set_error("graph instantiation failed: %s", cudaGetErrorString(ce));
+        return DQ_ERR_CUDA;
+      }
+      ctx->gkey = key;
+    }
+    DQ_CK(cudaEventRecord(ctx->gev[0], st));
+    DQ_CK(cudaStreamWaitEvent(ctx->gstream, ctx->gev[0], 0));
+    DQ_CK(cudaGraphLaunch(ctx->gexec, ctx->gstream));
+    DQ_CK(cudaEventRecord(ctx->gev[1], ctx->gstream));
+    DQ_CK(cudaStreamWaitEvent(st, ctx->gev[1], 0));
+    DQ_CK(cudaStreamSynchronize(ctx->gstream));
+  } else {
+    DQ_CK(enqueue(st));
+    DQ_CK(cudaStreamSynchronize(st));
+  }
 
   dq_status worst = DQ_OK;
   k = 0;
-  size_t si = 0;
   for (int i = 0; i < count; ++i) {
     dq_problem* P = probs[i];
     const size_t n = P->n, p = P->p, pn = std::max<size_t>(p, 1);
-    if (isnan(P->lmax_Q)) P->lmax_Q = hc[6 * k + 0];
-    if (isnan(P->normG2)) P->normG2 = hc[6 * k + 1];
+    if (isnan(P->lmax_Q)) P->lmax_Q = h_con[6 * k + 0];
+    if (isnan(P->normG2)) P->normG2 = h_con[6 * k + 1];
     P->has_state = true;
     const dq_outputs* o = outs ? &outs[i] : nullptr;
-    size_t off = 0;
-    if (o && o->memory == DQ_HOST) off = stages[si++].off;
+    const size_t off = stage_off[i];
     for (int b = 0; b < P->batch; ++b, ++k) {
-      fill_result(&results[k], hr[k], &hc[6 * k], cfgs[i]);
-      const dq_status st_i = (dq_status)hr[k].status;
-      if (st_i < 0 && st_i == DQ_ERR_INVALID)
-        set_error("instance %zu: invalid constants (DGM/DFGM need lmin_Q > 0)", k);
+      fill_result(&results[k], h_res[k], &h_con[6 * k], cfgs[i]);
+      const dq_status st_i = (dq_status)h_res[k].status;
+      if (st_i == DQ_ERR_INVALID) set_error("instance %zu: invalid constants (DGM/DFGM need lmin_Q > 0)", k);
       if (st_i < 0 || worst < 0) worst = (st_i < worst) ? st_i : worst;
       else if (st_i > worst) worst = st_i;
       if (o && o->memory == DQ_HOST && st_i >= 0) {
-        const T* src = hs.data() + off + b * (2 * n + pn);
+        const T* src = h_stage + off + b * (2 * n + pn);
         if (o->x_last)
           for (size_t j = 0; j < n; ++j) ((double*)o->x_last)[b * n + j] = double(src[j]);
         if (o->x_avg)
@@ -186,9 +275,11 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
 }
 
 dq_status cta_solve_problems(dq_problem* const* probs, int count, const SolveCfg* cfgs,
-                             const dq_outputs* outs, dq_result* results, int smem_cap, int threads) {
-  if (probs[0]->prec == DQ_FP64) return run<double>(probs, count, cfgs, outs, results, smem_cap, threads);
-  return run<float>(probs, count, cfgs, outs, results, smem_cap, threads);
+                             const dq_outputs* outs, dq_result* results, int smem_cap, int threads,
+                             bool graph) {
+  if (probs[0]->prec == DQ_FP64)
+    return run<double>(probs, count, cfgs, outs, results, smem_cap, threads, graph);
+  return run<float>(probs, count, cfgs, outs, results, smem_cap, threads, graph);
 }
 
 }  // namespace dq

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -52,6 +53,15 @@ struct dq_context {
   bool profile = false;
   int64_t gemv_launches = 0;
   double gemv_ms = 0.0, gemv_bytes = 0.0;
+  // pinned staging and the captured graph of the last persistent launch
+  void* pinned = nullptr;
+  size_t pinned_bytes = 0;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec = nullptr;
+  uint64_t gkey = 0;
+  // autotuned CTA-engine configurations: size-histogram signature -> (threads, smem cap)
+  std::map<std::string, std::pair<int, int>> tuned;
 };
 
 struct dq_problem {
@@ -79,6 +89,7 @@ dq_status tc_solve(dq_problem* prob, const SolveCfg& c, const dq_outputs* out, d
 void tc_free(TcWs* w);
 dq_status cta_solve_problems(dq_problem* const* probs, int count, const SolveCfg* cfgs,
                              const dq_outputs* outs, dq_result* results, int smem_cap,
-                             int threads);
+                             int threads, bool graph);
+std::string cta_signature(dq_problem* const* probs, int count);
 void fill_result(dq_result* r, const DevResult& d, const double* consts, const SolveCfg& c);
 }  // namespace dq

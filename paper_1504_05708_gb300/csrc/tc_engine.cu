@@ -7,13 +7,6 @@
 
 namespace dq {
 
-struct TcWs {};
-void tc_free(TcWs* w) { delete w; }
-
-dq_status tc_solve(dq_problem*, const SolveCfg&, const dq_outputs*, dq_result*) {
-  set_error("tensor-core engine not available");
-  return DQ_ERR_INVALID;
-}
 
 // Pack an R x K row-major float matrix (rows >= R_valid and cols >= K_valid
 // are zero) into bf16 hi and lo tiles of the K-major no-swizzle layout with

@@ -74,7 +74,7 @@ class Stats(ctypes.Structure):
 SYMBOLS = ("dq_context_create", "dq_context_destroy", "dq_problem_create", "dq_problem_set_vectors",
            "dq_problem_constants", "dq_problem_destroy", "dq_solve", "dq_solve_many", "dq_serve_start",
            "dq_submit", "dq_poll", "dq_serve_stop", "dq_context_profile", "dq_context_stats",
-           "dq_test_tc_gemm", "dq_last_error", "dq_version")
+           "dq_autotune", "dq_test_tc_gemm", "dq_last_error", "dq_version")
 
 _lib = None
 
@@ -113,6 +113,8 @@ def lib(build_if_needed: bool = True):
     L.dq_serve_stop.argtypes = [vp]
     L.dq_test_tc_gemm.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, vp]
+    L.dq_autotune.argtypes = [P(vp), ctypes.c_int32, P(SolveOpts), ctypes.c_int32, P(ctypes.c_int32),
+                              P(ctypes.c_int32)]
     L.dq_context_profile.argtypes = [vp, ctypes.c_int32]
     L.dq_context_stats.argtypes = [vp, P(Stats), ctypes.c_int32]
     for name in SYMBOLS[:-2]:
@@ -288,6 +290,16 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def autotune(problems, o_list, sample=256):
+    """dq_autotune: pick (threads, smem cap) for this mix; returns the choice."""
+    cnt = len(problems)
+    hs = (ctypes.c_void_p * cnt)(*[p.h.value for p in problems])
+    os_ = (SolveOpts * cnt)(*o_list)
+    t, s = ctypes.c_int32(), ctypes.c_int32()
+    check(lib().dq_autotune(hs, cnt, os_, sample, ctypes.byref(t), ctypes.byref(s)), (OK,))
+    return t.value, s.value
 
 
 def solve_many(problems, o_list, *, device_outs=None):

@@ -69,7 +69,7 @@ def test_fp64_certificate_mode_parity(ctx, alg):
 def test_fp32_eps_optimal_and_close(ctx, alg):
     from paper_1504_05708_gb300 import duquad as D
     from oracle.kkt import solve_kkt
-    inst = W.single_dense(n=12, p=6, seed=31, g_scale=0.02, box=0.3, lam_lo=1.0, lam_hi=50.0)
+    inst = W.single_dense(n=6, p=4, seed=31, g_scale=0.02, box=0.3, lam_lo=1.0, lam_hi=50.0)
     xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
     eps = 1e-3
     P = gpu_problem(ctx, inst, D.FP32)

@@ -139,7 +139,7 @@ def mpc_batch(batch=16384, nx=12, nu=4, N=25, seed=2, x0_seed=None):
     Q = Gamma' Qbar Gamma + Rbar, q = Gamma' Qbar (Phi x0 - x_ref),
     G = [Gamma; -Gamma], g = [Phi x0 - b; -Phi x0 - b], box |u| <= 1,
     b = 1.05 max over the batch of max_k ||A^k x0||_inf (u = 0 strictly feasible),
-    x_ref = 1.2 b on state 1 and 0 elsewhere (so state bounds become active).
+    x_ref = 2 b on state 1 and 0 elsewhere (so state bounds become active).
     Returns dict(Q (n,n), G (p,n), qs (B,n), gs (B,p), lb, ub, lmin_Q, x0s)."""
     m = mpc_matrices(nx, nu, N, seed)
     rng = np.random.default_rng(seed + 1000 if x0_seed is None else x0_seed)
@@ -148,7 +148,7 @@ def mpc_batch(batch=16384, nx=12, nu=4, N=25, seed=2, x0_seed=None):
     free = x0s @ Phi.T                      # (B, N*nx) free response
     b = 1.05 * np.abs(free).max()
     x_ref = np.zeros(N * nx)
-    x_ref[0::nx] = 1.2 * b
+    x_ref[0::nx] = 2.0 * b
     Q = Gam.T @ m["Qbar"] @ Gam + m["Rbar"]
     Q = 0.5 * (Q + Q.T)
     qs = (free - x_ref[None, :]) @ m["Qbar"] @ Gam
