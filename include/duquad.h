@@ -144,6 +144,9 @@ typedef struct {
  * stream `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
  * Errors: DQ_ERR_INVALID (bad device), DQ_ERR_CUDA. */
 dq_status dq_context_create(int device, void *cuda_stream, dq_context **out);
+/* Stops serving and releases the context; when problem handles of the
+ * context still exist the release happens when the last one is destroyed
+ * (the context must not be used after this call either way). */
 dq_status dq_context_destroy(dq_context *ctx);
 
 /* Create a problem handle.  memory = DQ_HOST: the arrays are copied to the

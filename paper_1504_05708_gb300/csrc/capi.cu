@@ -249,9 +249,7 @@ dq_status dq_context_create(int device, void* cuda_stream, dq_context** out) {
 
 dq_status dq_serve_stop(dq_context* ctx);
 
-dq_status dq_context_destroy(dq_context* ctx) {
-  if (!ctx) return DQ_OK;
-  if (ctx->serve) dq_serve_stop(ctx);
+static void context_free(dq_context* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
@@ -261,6 +259,16 @@ dq_status dq_context_destroy(dq_context* ctx) {
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->scratch) cudaFree(ctx->scratch);
   delete ctx;
+}
+
+dq_status dq_context_destroy(dq_context* ctx) {
+  if (!ctx) return DQ_OK;
+  if (ctx->serve) dq_serve_stop(ctx);
+  if (ctx->live_problems > 0) {  // freed when the last problem handle goes
+    ctx->destroy_requested = true;
+    return DQ_OK;
+  }
+  context_free(ctx);
   return DQ_OK;
 }
 
@@ -317,6 +325,7 @@ dq_status dq_problem_create(dq_context* ctx, const dq_problem_desc* d, dq_proble
   DQ_CK(cudaSetDevice(ctx->device));
   dq_problem* P = new dq_problem();
   P->ctx = ctx;
+  ++ctx->live_problems;
   P->n = d->n;
   P->p = d->p;
   P->batch = d->batch;
@@ -427,7 +436,9 @@ dq_status dq_problem_destroy(dq_problem* P) {
     if (b) cudaFree(b);
   if (P->gws) grid_free(P->gws);
   if (P->tws) tc_free(P->tws);
+  dq_context* ctx = P->ctx;
   delete P;
+  if (--ctx->live_problems == 0 && ctx->destroy_requested) context_free(ctx);
   return DQ_OK;
 }
 

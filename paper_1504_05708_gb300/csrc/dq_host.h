@@ -62,6 +62,10 @@ struct dq_context {
   uint64_t gkey = 0;
   // autotuned CTA-engine configurations: size-histogram signature -> (threads, smem cap)
   std::map<std::string, std::pair<int, int>> tuned;
+  // lifetime: problems keep their context alive; a destroy requested while
+  // problems exist is carried out when the last one is destroyed
+  int live_problems = 0;
+  bool destroy_requested = false;
 };
 
 struct dq_problem {

@@ -26,10 +26,14 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "dq_host.h"
+#include "grid_v2.cuh"
 
 namespace dq {
 
@@ -400,6 +404,16 @@ struct GridWs {
   void *c, *tn, *w, *whi, *wlo, *mu, *lam, *lamp, *ul, *uavg, *pv, *pw, *pt;
   double *usum, *dQ, *dG, *gwh, *gwl;
   int blocks = 0;
+  // single-pass (v2) layout: packed upper triangle of Q and partial sums
+  void* v2mem = nullptr;
+  float* Qp = nullptr;
+  long long* qoff = nullptr;
+  int* rows = nullptr;       // qrow (nQ + 1) then grow (nG + 1)
+  float* dotQ = nullptr;
+  float4* parts = nullptr;
+  int v2_ctas = 0;
+  bool v2_ready = false;
+  std::vector<long long> hoff;  // host copy of the packed-row offsets
 };
 
 void grid_free(GridWs* w) {
@@ -408,6 +422,7 @@ void grid_free(GridWs* w) {
   if (w->ctrl) cudaFree(w->ctrl);
   if (w->hctrl) cudaFreeHost(w->hctrl);
   if (w->partials) cudaFree(w->partials);
+  if (w->v2mem) cudaFree(w->v2mem);
   for (auto& e : w->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : w->evpool) cudaEventDestroy(e);
@@ -549,6 +564,86 @@ struct GridRun {
     return DQ_OK;
   }
 
+  // ---- single-pass iteration (grid_v2.cuh): setup and launch
+  bool use_v2 = false;
+  int v2_nQ = 0, v2_nG = 0, v2_npt = 0;
+  size_t v2_smem = 0;
+
+  dq_status v2_setup(bool aug) {
+    const int n4 = n / 4, B2 = P->ctx->num_sms;
+    if (!W->v2_ready) {
+      W->hoff.resize(n + 1);
+      long long acc = 0;
+      for (int i = 0; i < n; ++i) {
+        W->hoff[i] = acc;
+        acc += n - (i & ~3);
+      }
+      W->hoff[n] = acc;
+      auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+      const size_t bQ = a256((size_t)acc * 4), bO = a256((size_t)n * 8), bR = a256((size_t)(B2 + 2) * 4),
+                   bD = a256((size_t)n * 4), bP = a256((size_t)B2 * n4 * 16);
+      if (cudaMalloc(&W->v2mem, bQ + bO + bR + bD + bP) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("packed-Q allocation failed");
+        return DQ_ERR_NOMEM;
+      }
+      char* b = (char*)W->v2mem;
+      W->Qp = (float*)b;
+      W->qoff = (long long*)(b + bQ);
+      W->rows = (int*)(b + bQ + bO);
+      W->dotQ = (float*)(b + bQ + bO + bR);
+      W->parts = (float4*)(b + bQ + bO + bR + bD);
+      DQ_CK(cudaMemcpyAsync(W->qoff, W->hoff.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+      k_pack_upper<<<std::min(n, 8192), 256, 0, st>>>((const float*)Q(), n, W->qoff, W->Qp);
+      ++P->ctx->launches;
+      DQ_CK(cudaGetLastError());
+      W->v2_ready = true;
+    }
+    // CTA roles in proportion to the bytes each matrix contributes
+    const double bq = double(W->hoff[n]), bg = aug ? double(p) * n : 0.0;
+    int nQ = aug && p > 0 ? (int)lround(B2 * bq / (bq + bg)) : B2;
+    nQ = std::max(1, std::min(nQ, aug && p > 0 ? B2 - 1 : B2));
+    const int nG = aug && p > 0 ? B2 - nQ : 0;
+    std::vector<int> rows(nQ + 1 + nG + 1);
+    rows[0] = 0;
+    int r = 0, maxq = 0;
+    for (int c = 1; c < nQ; ++c) {
+      const double target = bq * c / nQ;
+      while (r < n && double(W->hoff[r]) < target) ++r;
+      rows[c] = r;
+    }
+    rows[nQ] = n;
+    for (int c = 0; c < nQ; ++c) maxq = std::max(maxq, rows[c + 1] - rows[c]);
+    for (int c = 0; c <= nG; ++c) rows[nQ + 1 + c] = (int)((long long)p * c / std::max(nG, 1));
+    DQ_CK(cudaMemcpyAsync(W->rows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, st));
+    v2_nQ = nQ;
+    v2_nG = nG;
+    v2_npt = std::max(2, ((n4 + V2_THREADS - 1) / V2_THREADS + 1) / 2 * 2);
+    v2_smem = std::max<size_t>(nG > 0 ? 2 * (size_t)n4 * 16 : 0, (size_t)maxq * 4) + 256;
+    return DQ_OK;
+  }
+
+  cudaError_t v2_pass(const V2Args& A) {
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kern) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v2_smem);
+      if (e == cudaSuccess) {
+        kern<<<v2_nQ + v2_nG, V2_THREADS, v2_smem, st>>>(A);
+        e = cudaGetLastError();
+      }
+    };
+    switch (v2_npt) {
+      case 2: go(k_v2_pass<2>); break;
+      case 4: go(k_v2_pass<4>); break;
+      case 6: go(k_v2_pass<6>); break;
+      case 8: go(k_v2_pass<8>); break;
+      case 10: go(k_v2_pass<10>); break;
+      default: go(k_v2_pass<12>); break;
+    }
+    ++P->ctx->launches;
+    return e;
+  }
+
   // Copy (x, Qx, Gx) from slot `from` of chain S to slots 0 and 2 of chain D.
   cudaError_t seed_chain(void* const* Sx, void* const* SQ, void* const* SG, int from, void* const* Dx,
                          void* const* DQ_, void* const* DG) {
@@ -605,6 +700,27 @@ struct GridRun {
       evn += 2;
       return ce;
     };
+    if (use_v2) {
+      dq_status s2 = v2_setup(aug);
+      if (s2 != DQ_OK) return s2;
+      if (aug && p > 0) {  // G' w(y^1), y^1 = x^0, for the first single-pass iteration
+        RowJob<T> J = job();
+        J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->tn);
+        J.vmode = VM_W; J.a0 = v(GX[0]); J.a1 = v(GX[0]); J.a2 = mu; J.a3 = g();
+        J.beta = T(0); J.rho = T(rho);
+        if ((e = rows<false>(J)) != cudaSuccess) {
+          set_error("fom setup: %s", cudaGetErrorString(e));
+          return DQ_ERR_CUDA;
+        }
+      }
+    }
+    auto next_beta = [&]() {
+      if (fgm_sigma) return beta_sigma;
+      const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+      const double bn = (theta - 1.0) / t1;
+      theta = t1;
+      return bn;
+    };
     while (k < kmax && kstop < 0) {
       // one chunk of up to m iterations, then (gap mode) the certificate
       const int kend = std::min(kmax, k + (fixed > 0 ? kmax : m));
@@ -612,6 +728,42 @@ struct GridRun {
         ++k;
         const int sx = slot_of(k - 1), sxp = slot_of(k - 2), sn = slot_of(k);
         const int* dn = fixed > 0 ? nullptr : &W->ctrl->inner_done;
+        if (use_v2) {
+          if constexpr (std::is_same<T, float>::value) {
+            const double bnext = next_beta();
+            V2Args A;
+            memset(&A, 0, sizeof(A));
+            A.n = n; A.p = p; A.n4 = n / 4; A.nQ = v2_nQ; A.nG = v2_nG;
+            A.qrow = W->rows; A.grow = W->rows + v2_nQ + 1; A.qoff = W->qoff; A.Qp = W->Qp; A.G = G();
+            A.x1 = v(X[sx]); A.x2 = v(X[sxp]); A.qx1 = v(QX[sx]); A.qx2 = v(QX[sxp]);
+            A.tn = aug ? v(W->tn) : nullptr; A.addv = aug ? q() : v(W->c); A.lb = lb(); A.ub = ub();
+            A.gx1 = v(GX[sx]); A.mu = mu; A.g = g();
+            A.beta_prev = (float)beta; A.beta_next = (float)bnext; A.L = (float)LL; A.rho = (float)rho; A.cone = cone;
+            A.xout = v(X[sn]); A.gxout = v(GX[sn]); A.dotQ = W->dotQ; A.partials = W->parts; A.done = dn;
+            const double bytes = 4.0 * (double(W->hoff[n]) + (aug ? double(p) * n : 0.0) + 10.0 * n + (aug ? 4.0 * p : 0));
+            if (P->ctx->profile) {
+              while ((int)W->evpool.size() < evn + 2) {
+                cudaEvent_t ev;
+                if ((e = cudaEventCreate(&ev)) != cudaSuccess) break;
+                W->evpool.push_back(ev);
+              }
+              cudaEventRecord(W->evpool[evn], st);
+              e = v2_pass(A);
+              cudaEventRecord(W->evpool[evn + 1], st);
+              recs.push_back({k, evn, bytes});
+              evn += 2;
+            } else {
+              e = v2_pass(A);
+            }
+            if (e != cudaSuccess) break;
+            k_v2_reduce<<<P->ctx->num_sms * 2, 256, 0, st>>>(W->parts, v2_nQ, v2_nG, n / 4, W->dotQ, v(QX[sn]),
+                                                             aug ? v(W->tn) : nullptr, dn);
+            ++P->ctx->launches;
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            beta = bnext;
+          }
+          continue;
+        }
         if (aug) {  // tn = G' [mu + rho (G y + g)]_+
           RowJob<T> J = job();
           J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->tn);
@@ -630,26 +782,20 @@ struct GridRun {
         const double bx = double(sizeof(T)) * (double(n) * n + (aug ? double(p) * n : 0.0) +
                                                (aug ? 10.0 : 9.0) * n + (aug ? p : 0));
         if ((e = timed(J, k, bx)) != cudaSuccess) break;
-        if (fgm_sigma) {
-          beta = beta_sigma;
-        } else {
-          const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
-          beta = (theta - 1.0) / t1;
-          theta = t1;
-        }
+        beta = next_beta();
       }
       if (e != cudaSuccess) break;
       if (fixed > 0) break;
       const int sc = slot_of(k);
       if (k % m == 0 || k >= kmax) {
         const T* add2 = nullptr;
-        if (aug) {  // gradient at x: G' [mu + rho (G x + g)]_+
+        if (aug) {  // gradient at x: G' [mu + rho (G x + g)]_+ (its own buffer: tn feeds the next pass)
           RowJob<T> J = job();
-          J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->tn);
+          J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->pw);
           J.vmode = VM_W; J.a0 = v(GX[sc]); J.a1 = v(GX[sc]); J.a2 = mu; J.a3 = g();
           J.beta = T(0); J.rho = T(rho); J.done = &W->ctrl->inner_done;
           if ((e = rows<false>(J)) != cudaSuccess) break;
-          add2 = v(W->tn);
+          add2 = v(W->pw);
         }
         k_cert<T><<<eb, 512, 0, st>>>(v(X[sc]), v(QX[sc]), aug ? q() : v(W->c), add2, lb(), ub(), n, LL, sigma,
                                        eps_in, k, kmax, W->partials, W->ctrl);
@@ -896,6 +1042,11 @@ static dq_status solve_T(dq_problem* P, GridWs* W, const SolveCfg& c, const dq_o
                                                                      : c.eps_out * sqrt(c.eps_out) / (8.0 * sqrt(2.0 * R.Ld)))
                              : c.eps_in;
   R.kd_plus = !(c.kd_literal && !(lmin > 0.0));
+  if constexpr (std::is_same<T, float>::value) {
+    // single-pass iteration when the rows fit its layout; DQ_GRID_SINGLE_PASS=0 selects the two-pass form
+    const char* ev = getenv("DQ_GRID_SINGLE_PASS");
+    R.use_v2 = (P->n % 4 == 0) && (P->n / 4 <= V2_THREADS * 12) && !(ev && ev[0] == '0');
+  }
   return R.solve(out, res);
 }
 

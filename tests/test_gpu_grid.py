@@ -105,3 +105,22 @@ def test_full_size_sampled_step(ctx):
                              lb=-np.ones(n), ub=np.ones(n))
     err = np.abs(x2[idx] - ref)
     assert err.max() <= 2e-5, err.max()
+
+
+@pytest.mark.parametrize("alg", ["DFGM", "ADFGM"])
+def test_single_pass_matches_two_pass(ctx, alg, monkeypatch):
+    """FP32: the single-pass iteration (packed upper triangle of Q, one read of G) and the
+    two-pass form give the same iterates at equal counts up to FP32 rounding, and both stay
+    within FP32 accuracy of the FP64 oracle (sizes with ragged CTA row ranges)."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=1028, p=517, seed=41, g_scale=0.05, lam_lo=1.0, lam_hi=30.0)
+    c = exact_constants(inst, alg)
+    o = gpu_opts_from(c, alg, fixed_inner=7, fixed_outer=3, engine=D.ENGINE_GRID)
+    P = gpu_problem(ctx, inst, D.FP32)
+    monkeypatch.setenv("DQ_GRID_SINGLE_PASS", "0")
+    x1, a1, l1, _ = P.solve(o)
+    monkeypatch.setenv("DQ_GRID_SINGLE_PASS", "1")
+    x2, a2, l2, _ = P.solve(o)
+    ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, inner_fixed=7, outer_fixed=3)
+    assert rel(x2, x1) <= 2e-5 and rel(a2, a1) <= 2e-5
+    assert rel(x2, ro.x_last) <= 1e-4 and rel(x1, ro.x_last) <= 1e-4
