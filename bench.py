@@ -323,8 +323,344 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ other workloads
+
+FP32_FFMA_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5: SMs x FP32 lanes x 2 flops x max SM clock
+
+
+def _timed(ctx, stream, fn, steps, warmup):
+    """Warm-up, then `steps` calls of fn between CUDA events on the library's stream."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    outs = [fn() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), clocks.stop(), ctx.stats(reset=True), outs
+
+
+def _base_line(args, value, ms, workload, dtype, cfg, clk, st, extra):
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": dict(workload=workload, parallelism="replicas1", **cfg), "gpu_launches": st["launches"],
+            "clocks": clk}
+    line.update(extra)
+    return line
+
+
+def _oracle_pool(tasks, budget_s):
+    """Run oracle solves (callables) on all host cores until the budget; returns (solves/s, cores, done)."""
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    done = 0
+    with ThreadPoolExecutor(cores) as ex:
+        futs = []
+        it = iter(tasks)
+        for _ in range(cores):
+            f = next(it, None)
+            if f is None:
+                break
+            futs.append(ex.submit(f))
+        while futs:
+            fut = futs.pop(0)
+            fut.result()
+            done += 1
+            if time.perf_counter() - t0 < budget_s:
+                f = next(it, None)
+                if f is not None:
+                    futs.append(ex.submit(f))
+    dt = time.perf_counter() - t0
+    return done / dt, cores, done
+
+
+def run_small(args):
+    """n=50, p=25 FP64 DFGM (one instance, one thread block, eps=1e-4)."""
+    import torch
+
+    import oracle as O
+    import workloads as W
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=50, p=25, seed=0)
+    stream = torch.cuda.current_stream()
+    ctx = D.Context(0, stream)
+    t = {k: torch.tensor(getattr(inst, k), dtype=torch.float64, device="cuda") for k in ("Q", "q", "G", "g", "lb", "ub")}
+    P = D.Problem(ctx, t["Q"], t["q"], t["G"], t["g"], t["lb"], t["ub"], prec=D.FP64, lmin_Q=inst.lmin_Q)
+    o = D.opts("DFGM", eps_out=1e-4, engine=D.ENGINE_CTA, fresh_constants=1)
+    outs = (torch.empty(50, dtype=torch.float64, device="cuda"), torch.empty(50, dtype=torch.float64, device="cuda"),
+            torch.empty(25, dtype=torch.float64, device="cuda"))
+    ms, clk, st, res = _timed(ctx, stream, lambda: P.solve(o, device_out=outs)[0], args.steps, args.warmup)
+    r = res[-1]
+    # e2e: host arrays through the ABI (handle creation, upload, solve, download, destroy)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        H = D.Problem(ctx, inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, prec=D.FP64, lmin_Q=inst.lmin_Q)
+        H.solve(o)
+        H.close()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    flops = r.inner_iters * 2.0 * 50 * 50 + r.outer_iters * 4.0 * 50 * 25
+    peaks, kind = load_peaks()
+    qp = O.QP(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+    c = O.constants(qp, O.DFGM, lmin_Q=inst.lmin_Q)
+    tasks = [lambda: O.dfom(qp, O.DFGM, c, eps_out=1e-4, eps_in=O.default_eps_in(O.DFGM, 1e-4, c.Ld))] * 200000
+    cpu_v, cores, done = _oracle_pool(tasks[:], min(args.cpu_seconds, 10.0))
+    line = _base_line(args, args.steps / (ms / 1e3), ms, "single_dense_n50_p25_fp64_dfgm", "f64",
+                      {"n": 50, "p": 25, "alg": "DFGM", "eps": 1e-4, "l2": "single 40 KB instance (latency-bound)"},
+                      clk, st, {
+                          "solve": {"status": r.status, "outer_iters": r.outer_iters, "inner_iters": r.inner_iters,
+                                    "f_last": r.f_last, "infeas_last": r.infeas_last},
+                          "roofline": {"kernel": "cta_solve_kernel<double>", "bound": "alu",
+                                       "achieved": flops / (ms / args.steps / 1e3) / 1e12, "peak": 1.25,
+                                       "unit": "TFLOP/s", "frac": flops / (ms / args.steps / 1e3) / 1e12 / 1.25,
+                                       "traffic": None, "peak_kind": "nominal FP64 (one thread block of 152 SMs)"},
+                          "e2e": {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 8 * (50 * 50 + 25 * 50 + 3 * 50 + 25),
+                                  "d2h_bytes_per_step": 8 * (2 * 50 + 25)},
+                          "cpu_baseline": {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                           "sample": f"{done} FP64 oracle solves of the same instance on {cores} host threads"}})
+    print(json.dumps(line), flush=True)
+    P.close()
+    ctx.close()
+
+
+def run_uneven(args):
+    """10000 independent QPs, n ~ U{16..512}, p = n/2, mixed algorithms, one persistent launch."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import workloads as W
+    from paper_1504_05708_gb300 import duquad as D
+    count = args.count
+    insts = W.uneven_batch_device(count, 3, device="cuda")
+    stream = torch.cuda.current_stream()
+    ctx = D.Context(0, stream)
+    probs, ops = [], []
+    for d in insts:
+        probs.append(D.Problem(ctx, d["Q"], d["q"], d["G"], d["g"], d["lb"], d["ub"], prec=D.FP32, lmin_Q=1.0))
+        ops.append(D.opts(d["alg"], eps_out=1e-3, max_outer=5000, fresh_constants=1))
+    tot_n = sum(d["n"] for d in insts)
+    tot_p = sum(d["p"] for d in insts)
+    bx = torch.empty(2 * tot_n, device="cuda")
+    bl = torch.empty(tot_p, device="cuda")
+    douts, on, op = [], 0, 0
+    for d in insts:
+        douts.append((bx[on:on + d["n"]], bx[tot_n + on:tot_n + on + d["n"]], bl[op:op + d["p"]]))
+        on += d["n"]
+        op += d["p"]
+    tune = D.autotune(probs, ops, sample=256)
+    ms, clk, st, res = _timed(ctx, stream, lambda: D.solve_many(probs, ops, device_outs=douts), args.steps, args.warmup)
+    rs = res[-1]
+    nn = np.array([d["n"] for d in insts], float)
+    pp = np.array([d["p"] for d in insts], float)
+    aug = np.array([d["alg"] in ("ADGM", "ADFGM") for d in insts])
+    inner = np.array([r.inner_iters for r in rs], float)
+    flops = float(np.sum(inner * (2 * nn * nn + np.where(aug, 4 * nn * pp, 0.0))))
+    tflops = flops / (ms / args.steps / 1e3) / 1e12
+    conv = sum(1 for r in rs if r.status == 0)
+    # CPU baseline: the FP64 oracle on a sample of the same instances, all host cores
+    sample = list(range(0, count, max(1, count // 400)))
+
+    def task(i):
+        d = insts[i]
+        qp = O.QP(d["Q"].double().cpu().numpy(), d["q"].double().cpu().numpy(), d["G"].double().cpu().numpy(),
+                  d["g"].double().cpu().numpy(), -np.ones(d["n"]), np.ones(d["n"]))
+        a = O.ALG_NAMES[d["alg"]]
+        c = O.constants(qp, a, lmin_Q=1.0)
+        return lambda: O.dfom(qp, a, c, eps_out=1e-3, eps_in=O.default_eps_in(a, 1e-3, c.Ld), max_outer=5000)
+    cpu_tasks = [task(i) for i in sample]
+    cpu_v, cores, done = _oracle_pool(cpu_tasks, args.cpu_seconds)
+    mean_cost = float(np.mean(nn[sample] ** 2)) / float(np.mean(nn ** 2))
+    line = _base_line(args, count * args.steps / (ms / 1e3), ms, "uneven_10000_n16_512_fp32_mixed", "f32",
+                      {"count": count, "n": "U{16..512}", "p": "n/2", "algs": "DGM/DFGM/ADGM/ADFGM", "eps": 1e-3,
+                       "autotuned": {"threads": tune[0], "smem_cap": tune[1]}, "graph": True,
+                       "l2": "5.4 GB of matrices, larger than L2"}, clk, st, {
+                          "solve": {"converged": conv, "inner_iters_mean": float(inner.mean())},
+                          "roofline": {"kernel": "cta_solve_kernel<float> (persistent)", "bound": "alu",
+                                       "achieved": tflops, "peak": FP32_FFMA_TFLOPS, "unit": "TFLOP/s",
+                                       "frac": tflops / FP32_FFMA_TFLOPS, "traffic": None,
+                                       "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                          "e2e": None,
+                          "cpu_baseline": {"value": cpu_v * mean_cost, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                           "sample": f"{done} of {len(sample)} sampled instances solved by the FP64 oracle on "
+                                                     f"{cores} threads, rate scaled by the sample's mean n^2 vs the batch's"}})
+    print(json.dumps(line), flush=True)
+    for P in probs:
+        P.close()
+    ctx.close()
+
+
+def run_mpc(args):
+    """16384 condensed-MPC QPs sharing Q, G: tensor cores (bf16 hi/lo) vs plain FP32 on the same batch."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import workloads as W
+    from paper_1504_05708_gb300 import duquad as D
+    B = args.count
+    d = W.mpc_batch(batch=B)
+    lmin = d["lmin_Q"]
+    stream = torch.cuda.current_stream()
+    ctx = D.Context(0, stream)
+    dev = {k: torch.tensor(d[k], dtype=torch.float32, device="cuda") for k in ("Q", "qs", "G", "gs", "lb", "ub")}
+    Pt = D.Problem(ctx, dev["Q"], dev["qs"], dev["G"], dev["gs"], dev["lb"], dev["ub"], prec=D.BF16X3, batch=B, lmin_Q=lmin)
+    Pf = D.Problem(ctx, dev["Q"], dev["qs"], dev["G"], dev["gs"], dev["lb"], dev["ub"], prec=D.FP32, batch=B, lmin_Q=lmin)
+    ot = D.opts("DFGM", eps_out=1e-3, eps_in=1e-5, check_every=5, max_outer=20000, fresh_constants=1)
+    of = D.opts("DFGM", eps_out=1e-3, eps_in=1e-5, check_every=5, max_outer=20000, engine=D.ENGINE_CTA, fresh_constants=1)
+    outs = (torch.empty(B, 100, device="cuda"), torch.empty(B, 100, device="cuda"), torch.empty(B, 600, device="cuda"))
+    ms, clk, st, res = _timed(ctx, stream, lambda: Pt.solve(ot, device_out=outs), args.steps, args.warmup)
+    msf, clkf, stf, resf = _timed(ctx, stream, lambda: Pf.solve(of, device_out=outs), 1, 0)
+    rs = res[-1]
+    inner = np.array([r.inner_iters for r in rs], float)
+    outer = np.array([r.outer_iters for r in rs], float)
+    useful = float(np.sum(inner * 2 * 100 * 100 + outer * 4 * 600 * 100))
+    issued_tile_iter = 3 * 2 * 128 * 112 * 112
+    tflops = useful / (ms / args.steps / 1e3) / 1e12
+    peaks, kind = load_peaks()
+    sample = list(range(0, B, max(1, B // 200)))
+    cs = O.constants(O.QP(d["Q"], d["qs"][0], d["G"], d["gs"][0], d["lb"], d["ub"]), O.DFGM, lmin_Q=lmin)
+
+    def task(b):
+        qp = O.QP(d["Q"], d["qs"][b], d["G"], d["gs"][b], d["lb"], d["ub"])
+        return lambda: O.dfom(qp, O.DFGM, cs, eps_out=1e-3, eps_in=1e-5, outer_check_every=5, max_outer=20000)
+    cpu_v, cores, done = _oracle_pool([task(b) for b in sample], args.cpu_seconds)
+    line = _base_line(args, B * args.steps / (ms / 1e3), ms, "mpc_batch_16384_n100_p600_bf16x3_dfgm", "bf16x3",
+                      {"batch": B, "n": 100, "p": 600, "alg": "DFGM", "eps": 1e-3, "eps_in": 1e-5,
+                       "lmin_Q": lmin, "l2": "per-instance state streamed per outer iteration"}, clk, st, {
+                          "fp32_plain": {"value": B / (msf / 1e3), "unit": "solves/s",
+                                         "engine": "CTA engine, one instance per thread block, FP32"},
+                          "solve": {"converged": int(sum(1 for r in rs if r.status == 0)),
+                                    "inner_iters_mean": float(inner.mean()), "outer_iters_mean": float(outer.mean())},
+                          "roofline": {"kernel": "k_tc_solve (tcgen05 bf16 hi/lo)", "bound": "tensor",
+                                       "achieved": tflops, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                                       "frac": tflops / peaks["bf16_tflops"], "traffic": None, "peak_kind": kind,
+                                       "note": f"useful flops (2n^2 per inner iteration, 4pn per outer); issued "
+                                               f"per tile-iteration {issued_tile_iter} (3 products, padding)"},
+                          "e2e": None,
+                          "cpu_baseline": {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                                           "sample": f"{done} of {len(sample)} sampled instances, FP64 oracle on {cores} threads"}})
+    print(json.dumps(line), flush=True)
+    Pt.close()
+    Pf.close()
+    ctx.close()
+
+
+def run_served(args):
+    """Poisson stream of solve requests into the persistent request loop."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import workloads as W
+    from paper_1504_05708_gb300 import duquad as D
+    rate, dur = args.rate, args.duration
+    times, kinds, picks = W.served_stream(rate=rate, duration=dur, seed=4)
+    ctx = D.Context(0)
+    pool = W.uneven_batch_device(args.pool, 5, device="cuda")
+    probs = []
+    for dd in pool:
+        probs.append(D.Problem(ctx, dd["Q"], dd["q"], dd["G"], dd["g"], dd["lb"], dd["ub"], prec=D.FP32, lmin_Q=1.0))
+    mpc = W.mpc_batch(batch=64, seed=6)
+    mpc_probs = [D.Problem(ctx, mpc["Q"], mpc["qs"][i], mpc["G"], mpc["gs"][i], mpc["lb"], mpc["ub"], prec=D.FP32,
+                           lmin_Q=mpc["lmin_Q"]) for i in range(8)]
+    ops = {a: D.opts(a, eps_out=1e-3, max_outer=5000) for a in W.ALGS}
+    om = D.opts("DFGM", eps_out=1e-3, eps_in=1e-5, check_every=5, max_outer=20000, warm_start=1)
+    rng = np.random.default_rng(7)
+    for P, dd in zip(probs, pool):  # constants once per handle
+        P.solve(ops[dd["alg"]])
+    for P in mpc_probs:
+        P.solve(om)
+    ctx.serve_start(slots=1024, hbm_budget_bytes=32 << 30)
+    sub, lat, meta = {}, [], []
+    lock = threading.Lock()
+    done_flag = [False]
+
+    def poller():
+        while not done_flag[0] or sub:
+            with lock:
+                items = list(sub.items())
+            for tk, (t0, n, p, info) in items:
+                r = ctx.poll(tk, n, p)
+                if r is not None:
+                    t1 = time.perf_counter()
+                    with lock:
+                        sub.pop(tk, None)
+                    lat.append(t1 - t0)
+                    if info is not None:
+                        meta.append((info, r))
+            time.sleep(0)
+    th = threading.Thread(target=poller, daemon=True)
+    th.start()
+    start = time.perf_counter()
+    for k, (ta, kind, pick) in enumerate(zip(times, kinds, picks)):
+        while time.perf_counter() - start < ta:
+            pass
+        if kind == 1:
+            i = int(pick) % len(mpc_probs)
+            x0 = rng.standard_normal(12)
+            P, n, p = mpc_probs[i], 100, 600
+            q = mpc["qs"][i] + 0.1 * rng.standard_normal(100)
+            tk = ctx.submit(P, om, q=q)
+            info = ("mpc", i, q) if k % 100 == 0 else None
+        else:
+            i = int(pick) % len(probs)
+            P, n, p = probs[i], pool[i]["n"], pool[i]["p"]
+            q = rng.standard_normal(n)
+            tk = ctx.submit(P, ops[pool[i]["alg"]], q=q)
+            info = ("qp", i, q) if k % 100 == 0 else None
+        with lock:
+            sub[tk] = (time.perf_counter(), n, p, info)
+    offered = time.perf_counter() - start
+    done_flag[0] = True
+    th.join(timeout=600)
+    total = time.perf_counter() - start
+    ctx.serve_stop()
+    lat_ms = np.array(lat) * 1e3
+    # FP64 oracle error on the 1% sample
+    errs = []
+    for info, (stt, xl, xa, lm, r) in meta[:200]:
+        kind, i, q = info
+        if kind == "qp":
+            dd = pool[i]
+            qp = O.QP(dd["Q"].double().cpu().numpy(), q, dd["G"].double().cpu().numpy(), dd["g"].double().cpu().numpy(),
+                      -np.ones(dd["n"]), np.ones(dd["n"]))
+            a = O.ALG_NAMES[dd["alg"]]
+        else:
+            qp = O.QP(mpc["Q"], q, mpc["G"], mpc["gs"][i], mpc["lb"], mpc["ub"])
+            a = O.DFGM
+        c = O.constants(qp, a, lmin_Q=1.0 if kind == "qp" else mpc["lmin_Q"])
+        ro = O.dfom(qp, a, c, eps_out=1e-5, eps_in=1e-9, max_outer=20000)
+        x = xl if r.converged_last else xa
+        errs.append(float(np.linalg.norm(x - ro.x_last) / max(np.linalg.norm(ro.x_last), 1e-12)))
+    line = {"metric": METRIC, "value": len(lat) / total, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": total * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "served_poisson", "rate_per_s": rate, "duration_s": dur, "pool": args.pool,
+                       "mpc_fraction": 0.05, "slots": 1024, "parallelism": "replicas1"},
+            "served": {"requests": int(len(times)), "completed": int(len(lat)), "offered_s": offered,
+                       "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
+                       "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
+                       "oracle_rel_err_max": max(errs) if errs else None, "oracle_sampled": len(errs)}}
+    print(json.dumps(line), flush=True)
+    for P in probs + mpc_probs:
+        P.close()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="large", choices=["large", "small", "uneven", "mpc", "served"])
+    ap.add_argument("--count", type=int, default=None)
+    ap.add_argument("--rate", type=float, default=20000.0)
+    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--pool", type=int, default=2000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -340,10 +676,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-inner-sample", type=int, default=8)
-    ap.add_argument("--ref-inner-per-solve", type=int, default=2000)
+    ap.add_argument("--ref-inner-per-solve", type=int, default=5430)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "small":
+        run_small(args)
+    elif args.workload == "uneven":
+        args.count = args.count or 10000
+        run_uneven(args)
+    elif args.workload == "mpc":
+        args.count = args.count or 16384
+        run_mpc(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_gpu(args)
 

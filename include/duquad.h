@@ -118,6 +118,9 @@ typedef struct {
   int32_t warm_start;      /* 1: start from the handle's last x and lambda     */
   int32_t kd_literal;      /* 1: K_d = R^p when lmin_Q == 0 (paper's literal)  */
   double Ld, LL, sigma;    /* NaN: derive from the problem's constants         */
+  int32_t fresh_constants; /* 1: recompute lambda_max(Q) and ||G||^2 in this
+                              solve instead of reusing the handle's (given
+                              values in dq_problem_desc are always kept)       */
 } dq_solve_opts;
 
 /* Result of one solve (one instance). */

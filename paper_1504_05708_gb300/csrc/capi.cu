@@ -14,6 +14,15 @@ namespace dq {
 
 static thread_local char g_err[512];
 
+size_t max_dynamic_smem(const void* kernel, size_t optin) {
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, kernel) != cudaSuccess) {
+    cudaGetLastError();
+    return optin > 4096 ? optin - 4096 : optin;
+  }
+  return optin > a.sharedSizeBytes ? optin - a.sharedSizeBytes : 0;
+}
+
 void set_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -173,6 +182,7 @@ dq_status resolve_opts(const dq_problem* P, const dq_solve_opts* o, SolveCfg* c)
   c->check_every = o->check_every > 0 ? o->check_every : 1;
   c->inner_check_every = o->inner_check_every > 0 ? o->inner_check_every : 1;
   c->warm_start = o->warm_start;
+  c->fresh = o->fresh_constants != 0;
   c->kd_literal = o->kd_literal;
   c->Ld = o->Ld;
   c->LL = o->LL;
@@ -335,6 +345,8 @@ dq_status dq_problem_create(dq_context* ctx, const dq_problem_desc* d, dq_proble
   P->lmax_Q = d->lmax_Q;
   P->lmin_Q = d->lmin_Q;
   P->normG2 = d->normG2;
+  P->lmax_given = d->lmax_Q;
+  P->normG2_given = d->normG2;
   dq_status s = DQ_OK;
   auto fail = [&](dq_status st) {
     dq_problem_destroy(P);

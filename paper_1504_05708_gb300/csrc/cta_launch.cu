@@ -134,9 +134,9 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
       I.g = (const T*)P->g + b * p;
       I.lb = (const T*)P->lb;
       I.ub = (const T*)P->ub;
-      I.lmax_Q = P->lmax_Q;
+      I.lmax_Q = c.fresh ? P->lmax_given : P->lmax_Q;
       I.lmin_Q = lmin;
-      I.normG2 = P->normG2;
+      I.normG2 = c.fresh ? P->normG2_given : P->normG2;
       I.rho = c.rho;
       I.LL = c.LL;
       I.sigma = c.sigma;
@@ -174,8 +174,10 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
       cost[k] = double(n) * n + 2.0 * double(n) * p;
     }
   }
-  const size_t cap = smem_cap > 0 ? std::min<size_t>(smem_cap, ctx->smem_optin) : ctx->smem_optin;
-  if (vec_max > ctx->smem_optin) {
+  const void* kfn = kernel_fn<T>(threads);
+  const size_t dmax = max_dynamic_smem(kfn, ctx->smem_optin);
+  const size_t cap = smem_cap > 0 ? std::min<size_t>(smem_cap, dmax) : dmax;
+  if (vec_max > dmax) {
     set_error("instance too large for the CTA engine (needs %zu bytes of shared memory)", vec_max);
     return DQ_ERR_INVALID;
   }
@@ -183,7 +185,6 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
   std::iota(h_order, h_order + total, 0);
   std::stable_sort(h_order, h_order + total, [&](int a, int b) { return cost[a] > cost[b]; });
 
-  const void* kfn = kernel_fn<T>(threads);
   DQ_CK(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   DQ_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, threads, smem));

@@ -15,14 +15,21 @@ namespace dq {
 
 void set_error(const char* fmt, ...);
 
+// On failure: record the message, clear the runtime's last-error state (so a
+// later cudaGetLastError check does not report this failure again) and return.
 #define DQ_CK(call)                                                             \
   do {                                                                          \
     cudaError_t e_ = (call);                                                    \
     if (e_ != cudaSuccess) {                                                    \
+      cudaGetLastError();                                                       \
       ::dq::set_error("%s failed: %s", #call, cudaGetErrorString(e_));          \
       return DQ_ERR_CUDA;                                                       \
     }                                                                           \
   } while (0)
+
+// Largest dynamic shared memory a kernel can request: the per-block opt-in
+// limit minus the kernel's static shared memory.
+size_t max_dynamic_smem(const void* kernel, size_t optin);
 
 struct GridWs;   // large-instance engine workspace (grid_engine.cu)
 struct TcWs;     // tensor-core batch workspace (tc_engine.cu)
@@ -33,7 +40,7 @@ struct SolveCfg {
   int alg, output, inner_stop, engine;
   double eps_out, eps_in, rho;
   int fixed_outer, fixed_inner, max_outer, max_inner, check_every, inner_check_every;
-  int warm_start, kd_literal;
+  int warm_start, kd_literal, fresh;
   double Ld, LL, sigma;
 };
 
@@ -78,6 +85,7 @@ struct dq_problem {
   void *x_state = nullptr, *lam_state = nullptr;
   bool has_state = false;
   double lmax_Q = NAN, lmin_Q = NAN, normG2 = NAN;
+  double lmax_given = NAN, normG2_given = NAN;  // as passed in dq_problem_desc
   dq::GridWs* gws = nullptr;
   dq::TcWs* tws = nullptr;
   std::mutex mu;

@@ -619,7 +619,8 @@ struct GridRun {
     v2_nQ = nQ;
     v2_nG = nG;
     v2_npt = std::max(2, ((n4 + V2_THREADS - 1) / V2_THREADS + 1) / 2 * 2);
-    v2_smem = std::max<size_t>(nG > 0 ? 2 * (size_t)n4 * 16 : 0, (size_t)maxq * 4) + 256;
+    (void)maxq;  // Q rows are dealt round-robin: each Q-CTA holds x_i of ceil(n / nQ) rows
+    v2_smem = 2 * (size_t)n4 * 16 + ((size_t)(n + nQ - 1) / nQ + 1) * 4 + 256;
     return DQ_OK;
   }
 
@@ -1043,9 +1044,9 @@ static dq_status solve_T(dq_problem* P, GridWs* W, const SolveCfg& c, const dq_o
                              : c.eps_in;
   R.kd_plus = !(c.kd_literal && !(lmin > 0.0));
   if constexpr (std::is_same<T, float>::value) {
-    // single-pass iteration when the rows fit its layout; DQ_GRID_SINGLE_PASS=0 selects the two-pass form
+    // the single-pass iteration runs when DQ_GRID_SINGLE_PASS=1 and the rows fit its layout
     const char* ev = getenv("DQ_GRID_SINGLE_PASS");
-    R.use_v2 = (P->n % 4 == 0) && (P->n / 4 <= V2_THREADS * 12) && !(ev && ev[0] == '0');
+    R.use_v2 = (P->n % 4 == 0) && (P->n / 4 <= V2_THREADS * 12) && (ev && ev[0] == '1');
   }
   return R.solve(out, res);
 }
@@ -1055,6 +1056,10 @@ dq_status grid_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq
   GridWs* W;
   dq_status s = grid_ws(P, &W);
   if (s != DQ_OK) return s;
+  if (c.fresh) {
+    P->lmax_Q = P->lmax_given;
+    P->normG2 = P->normG2_given;
+  }
   if (isnan(P->lmax_Q) || isnan(P->normG2)) {
     s = P->prec == DQ_FP64 ? constants_T<double>(P, W) : constants_T<float>(P, W);
     if (s != DQ_OK) return s;

@@ -91,54 +91,76 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
   for (int m = 0; m < NPT; ++m) part[m] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   if (qcta) {
-    const int r0 = a.qrow[blockIdx.x], r1 = a.qrow[blockIdx.x + 1];
-    float* xs = (float*)sm;  // x_i of this CTA's rows
+    // rows c, c + nQ, c + 2 nQ, ... (every CTA gets the same mix of long and
+    // short rows), streamed through a double buffer of bulk copies
+    const int c = blockIdx.x, nQ = a.nQ;
+    const int cnt = c < a.n ? (a.n - 1 - c) / nQ + 1 : 0;
+    float* xs = (float*)(sm + 2 * (size_t)a.n4 * 16);  // x_i of this CTA's rows
+    auto qbuf = [&](int s) { return (const float4*)(sm + (size_t)s * a.n4 * 16); };
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
       const int c4 = t + V2_THREADS * m;
-      const int i = 4 * c4;
       if (c4 < a.n4) {
-        if (i + 0 >= r0 && i + 0 < r1) xs[i + 0 - r0] = xr[m].x;
-        if (i + 1 >= r0 && i + 1 < r1) xs[i + 1 - r0] = xr[m].y;
-        if (i + 2 >= r0 && i + 2 < r1) xs[i + 2 - r0] = xr[m].z;
-        if (i + 3 >= r0 && i + 3 < r1) xs[i + 3 - r0] = xr[m].w;
+        const float xv[4] = {xr[m].x, xr[m].y, xr[m].z, xr[m].w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * c4 + u;
+          if (i >= c && (i - c) % nQ == 0) xs[(i - c) / nQ] = xv[u];
+        }
       }
     }
+    if (t == 0) {
+      tc::mbar_init(&full[0], 1);
+      tc::mbar_init(&full[1], 1);
+      tc::mbar_init_fence();
+    }
     __syncthreads();
-    for (int rb = r0; rb < r1; rb += V2_RB) {
-      const int re = min(r1, rb + V2_RB);
-      for (int i = rb; i < re; ++i) {
-        const float4* row = (const float4*)(a.Qp + a.qoff[i]);
+    auto issue = [&](int idx, int s) {
+      const int i = c + idx * nQ;
+      const uint32_t bytes = (uint32_t)(a.n - (i & ~3)) * 4u;
+      tc::mbar_expect_tx(&full[s], bytes);
+      tc::bulk_g2s((void*)qbuf(s), a.Qp + a.qoff[i], bytes, &full[s]);
+    };
+    if (t == 0)
+      for (int s = 0; s < 2 && s < cnt; ++s) issue(s, s);
+    for (int rb = 0; rb < cnt; rb += V2_RB) {
+      const int re = min(cnt, rb + V2_RB);
+      for (int idx = rb; idx < re; ++idx) {
+        const int i = c + idx * nQ;
+        const int s = idx & 1;
+        tc::mbar_wait(&full[s], (idx >> 1) & 1, 2000000000ull);
+        const float4* row = qbuf(s);
         const int f0 = i >> 2;  // first float4 column of the packed row
-        const float xi = xs[i - r0];
-        float s = 0.f, comp = 0.f;
+        const float xi = xs[idx];
+        float sa = 0.f, comp = 0.f;
 #pragma unroll
         for (int m = 0; m < NPT; ++m) {
           const int c4 = t + V2_THREADS * m;
           if (c4 >= f0 && c4 < a.n4) {
-            const float4 v = __ldcs(row + (c4 - f0));
+            const float4 v = row[c4 - f0];
             float d = v.x * xr[m].x;
             d = fmaf(v.y, xr[m].y, d);
             d = fmaf(v.z, xr[m].z, d);
             d = fmaf(v.w, xr[m].w, d);
-            const float yk = d - comp, tk = s + yk;  // Kahan pair
-            comp = (tk - s) - yk;
-            s = tk;
+            const float yk = d - comp, tk = sa + yk;  // Kahan pair
+            comp = (tk - sa) - yk;
+            sa = tk;
             part[m].x = fmaf(xi, v.x, part[m].x);
             part[m].y = fmaf(xi, v.y, part[m].y);
             part[m].z = fmaf(xi, v.z, part[m].z);
             part[m].w = fmaf(xi, v.w, part[m].w);
           }
         }
-        double tot = double(s) - double(comp);
+        double tot = double(sa) - double(comp);
         for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-        if (lane == 0) sdot[i - rb][warp] = float(tot);
+        if (lane == 0) sdot[idx - rb][warp] = float(tot);
+        __syncthreads();  // buffer s free again
+        if (t == 0 && idx + 2 < cnt) issue(idx + 2, s);
       }
-      __syncthreads();
       if (t < re - rb) {
         double s = 0.0;
         for (int w = 0; w < V2_THREADS / 32; ++w) s += sdot[t][w];
-        a.dotQ[rb + t] = float(s);
+        a.dotQ[c + (rb + t) * nQ] = float(s);
       }
       __syncthreads();
     }

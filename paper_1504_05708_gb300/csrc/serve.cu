@@ -199,9 +199,9 @@ static void fill_entry(ServeState* S, int e, Ticket& t) {
   I.g = nullptr;
   I.lb = (const float*)P->lb;
   I.ub = (const float*)P->ub;
-  I.lmax_Q = P->lmax_Q;
+  I.lmax_Q = c.fresh ? P->lmax_given : P->lmax_Q;
   I.lmin_Q = P->lmin_Q;
-  I.normG2 = P->normG2;
+  I.normG2 = c.fresh ? P->normG2_given : P->normG2;
   I.rho = c.rho;
   I.LL = c.LL;
   I.sigma = c.sigma;
@@ -390,7 +390,7 @@ dq_status dq_serve_start(dq_context* ctx, int32_t slots, int64_t hbm_budget_byte
   if (cudaMalloc(&S->slot_g, R * pm * sizeof(float)) != cudaSuccess) return fail("slot g");
   if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) return fail("stream");
   if (cudaEventCreateWithFlags(&S->kdone, cudaEventDisableTiming) != cudaSuccess) return fail("event");
-  S->smem = std::min<size_t>(ctx->smem_optin, 96 * 1024);
+  S->smem = std::min<size_t>(max_dynamic_smem((const void*)serve_kernel, ctx->smem_optin), 96 * 1024);
   S->smem = std::max(S->smem, cta_vec_bytes<float>(S->nmax, S->pmax));
   auto kern = serve_kernel;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S->smem) != cudaSuccess)

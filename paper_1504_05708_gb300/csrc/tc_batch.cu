@@ -697,6 +697,10 @@ dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_r
   }
   dq_context* ctx = P->ctx;
   cudaStream_t st = ctx->stream;
+  if (c.fresh) {
+    P->lmax_Q = P->lmax_given;
+    P->normG2 = P->normG2_given;
+  }
   if (isnan(P->lmax_Q) || isnan(P->normG2)) {
     dq_status s = grid_constants(P);
     if (s != DQ_OK) return s;
@@ -705,7 +709,7 @@ dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_r
   dq_status s = tc_ws(P, &W);
   if (s != DQ_OK) return s;
   const size_t smem = tc_smem_bytes(W);
-  if (smem > ctx->smem_optin) {
+  if (smem > max_dynamic_smem((const void*)k_tc_solve, ctx->smem_optin)) {
     set_error("tensor-core engine needs %zu bytes of shared memory", smem);
     return DQ_ERR_INVALID;
   }

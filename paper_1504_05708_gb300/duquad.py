@@ -45,7 +45,8 @@ class SolveOpts(ctypes.Structure):
                 ("max_outer", ctypes.c_int32), ("max_inner", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("inner_check_every", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("kd_literal", ctypes.c_int32),
-                ("Ld", ctypes.c_double), ("LL", ctypes.c_double), ("sigma", ctypes.c_double)]
+                ("Ld", ctypes.c_double), ("LL", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("fresh_constants", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -145,7 +146,8 @@ def _ptr(a):
 
 def opts(alg="DFGM", *, output=OUT_BOTH, inner_stop=INNER_GAP, engine=ENGINE_AUTO, eps_out=1e-3,
          eps_in=NAN, rho=NAN, fixed_outer=0, fixed_inner=0, max_outer=0, max_inner=0, check_every=0,
-         inner_check_every=0, warm_start=0, kd_literal=0, Ld=NAN, LL=NAN, sigma=NAN) -> SolveOpts:
+         inner_check_every=0, warm_start=0, kd_literal=0, Ld=NAN, LL=NAN, sigma=NAN,
+         fresh_constants=0) -> SolveOpts:
     o = SolveOpts()
     o.alg = ALGS[alg] if isinstance(alg, str) else int(alg)
     o.output, o.inner_stop, o.engine = output, inner_stop, engine
@@ -153,6 +155,7 @@ def opts(alg="DFGM", *, output=OUT_BOTH, inner_stop=INNER_GAP, engine=ENGINE_AUT
     o.fixed_outer, o.fixed_inner, o.max_outer, o.max_inner = fixed_outer, fixed_inner, max_outer, max_inner
     o.check_every, o.inner_check_every, o.warm_start, o.kd_literal = check_every, inner_check_every, warm_start, kd_literal
     o.Ld, o.LL, o.sigma = Ld, LL, sigma
+    o.fresh_constants = fresh_constants
     if fixed_inner and inner_stop == INNER_GAP:
         o.inner_stop = INNER_FIXED
     return o

@@ -55,8 +55,11 @@ def test_mpc_eps_optimal_vs_oracle(ctx, alg):
     lmin = float(np.linalg.eigvalsh(d["Q"])[0]) * 0.999
     eps = 1e-3
     P = _problem(ctx, d, D.BF16X3)
-    xl, xa, lam, res = P.solve(D.opts(alg, eps_out=eps, eps_in=1e-5, check_every=5, max_outer=20000))
-    assert all(r.status == 0 for r in res), [r.status for r in res][:10]
+    # DGM's O(L_d R_d^2 / eps) outer bound (Sec. 4) is far above DFGM's: give it room
+    max_outer = 200000 if alg == "DGM" else 20000
+    xl, xa, lam, res = P.solve(D.opts(alg, eps_out=eps, eps_in=1e-5, check_every=5, max_outer=max_outer))
+    bad = [(b, r.status, r.outer_iters) for b, r in enumerate(res) if r.status != 0]
+    assert not bad, bad[:10]
     for b in (0, 64, B - 1):
         qp = O.QP(d["Q"], d["qs"][b], d["G"], d["gs"][b], d["lb"], d["ub"])
         c = O.constants(qp, O.DFGM, lmin_Q=lmin)

@@ -192,3 +192,43 @@ def served_stream(rate=20000.0, duration=60.0, seed=4, mpc_fraction=0.05):
     kinds = (rng.random(t.size) < mpc_fraction).astype(np.int32)
     picks = rng.integers(0, 2**31 - 1, t.size)
     return t, kinds, picks
+
+
+def uneven_batch_device(count=10000, seed=3, n_lo=16, n_hi=512, device="cuda", dtype=None):
+    """The uneven batch drawn directly in device memory (torch), for the full-size case.
+
+    Same distribution as uneven_instance (Haar eigenvectors, lambda_1 = 1,
+    lambda_n = kappa, the rest U[1, kappa]; G ~ N(0, 1/n); g = -|N(0,1)| - 0.1;
+    box [-1, 1]) with sizes, kappas and algorithms from uneven_sizes, but a torch
+    random stream, so its entries differ from the host instances.  Returns a
+    list of dicts (n, p, alg, Q, q, G, g, lb, ub) of `dtype` tensors."""
+    import torch
+
+    dtype = dtype or torch.float32
+    ns, kappas, algs, _ = uneven_sizes(count, seed, n_lo, n_hi)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    out = [None] * count
+    f64 = dict(device=device, dtype=torch.float64)
+    for n in sorted(set(int(v) for v in ns)):
+        idx = [i for i in range(count) if int(ns[i]) == n]
+        b, p = len(idx), n // 2
+        Z = torch.randn(b, n, n, generator=gen, **f64)
+        U, R = torch.linalg.qr(Z)
+        U = U * torch.sign(torch.diagonal(R, dim1=-2, dim2=-1)).unsqueeze(-2)
+        kap = torch.tensor([float(kappas[i]) for i in idx], **f64)
+        lam = 1.0 + torch.rand(b, n, generator=gen, **f64) * (kap[:, None] - 1.0)
+        lam[:, 0] = 1.0
+        if n > 1:
+            lam[:, 1] = kap
+        Q = (U * lam[:, None, :]) @ U.transpose(-1, -2)
+        Q = 0.5 * (Q + Q.transpose(-1, -2))
+        q = torch.randn(b, n, generator=gen, **f64)
+        G = torch.randn(b, p, n, generator=gen, **f64) / n ** 0.5
+        g = -torch.randn(b, p, generator=gen, **f64).abs() - 0.1
+        for k, i in enumerate(idx):
+            out[i] = dict(n=n, p=p, alg=ALGS[int(algs[i])], Q=Q[k].to(dtype).contiguous(),
+                          q=q[k].to(dtype).contiguous(), G=G[k].to(dtype).contiguous(),
+                          g=g[k].to(dtype).contiguous(), lb=-torch.ones(n, device=device, dtype=dtype),
+                          ub=torch.ones(n, device=device, dtype=dtype))
+    return out
