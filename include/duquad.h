@@ -187,6 +187,30 @@ dq_status dq_solve(dq_problem *prob, const dq_solve_opts *opts, const dq_outputs
 dq_status dq_solve_many(dq_problem *const *probs, int32_t count, const dq_solve_opts *opts,
                         const dq_outputs *out, dq_result *results);
 
+/* Solve one FP64 or FP32 instance without allocating memory.  The paper has
+ * no counterpart: this is for callers that cannot allocate device memory
+ * while running -- a real-time loop (e.g. model-predictive control solving
+ * one QP per sampling period) whose timing must not depend on an allocator,
+ * or a process whose memory pool has already reserved the GPU, so that a
+ * further cudaMalloc fails.  It runs the same whole-solve-per-thread-block
+ * kernel as dq_solve's CTA engine on the caller's device arrays and keeps
+ * its scratch (instance descriptor, work-queue counter, result, constants and
+ * a transposed copy of G) in one fixed 8 MiB device array inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ * desc: memory must be DQ_DEVICE, batch 1, prec DQ_FP64 or DQ_FP32 (arrays of
+ * double or float).  out (nullable): DQ_DEVICE arrays of the same type.
+ * Limits: n * p elements of G must fit the scratch (8 MiB minus 4 KiB:
+ * n * p <= 1048064 for FP64, 2096128 for FP32) and the instance's vectors one
+ * thread block's shared memory; otherwise DQ_ERR_INVALID with a message.
+ * No warm start.  The first call on a device looks up the scratch's address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call shares the one scratch array, so
+ * calls whose GPU work overlaps (other streams or threads on the same device)
+ * race: serialise them.  stream: cudaStream_t (NULL = legacy default);
+ * synchronises it before returning. */
+dq_status dq_solve_noalloc(int device, const dq_problem_desc *desc, const dq_solve_opts *opts,
+                           const dq_outputs *out, dq_result *result, void *cuda_stream);
+
 /* Autotune the launch shape dq_solve_many uses for this mix of problems:
  * times short fixed-count solves (2 outer x 25 inner iterations) of up to
  * `sample` instances spread over the mix under each candidate block size

@@ -75,7 +75,7 @@ class Stats(ctypes.Structure):
 SYMBOLS = ("dq_context_create", "dq_context_destroy", "dq_problem_create", "dq_problem_set_vectors",
            "dq_problem_constants", "dq_problem_destroy", "dq_solve", "dq_solve_many", "dq_serve_start",
            "dq_submit", "dq_poll", "dq_serve_stop", "dq_context_profile", "dq_context_stats",
-           "dq_autotune", "dq_test_tc_gemm", "dq_last_error", "dq_version")
+           "dq_autotune", "dq_solve_noalloc", "dq_test_tc_gemm", "dq_last_error", "dq_version")
 
 _lib = None
 
@@ -116,6 +116,7 @@ def lib(build_if_needed: bool = True):
                                   ctypes.c_int32, vp]
     L.dq_autotune.argtypes = [P(vp), ctypes.c_int32, P(SolveOpts), ctypes.c_int32, P(ctypes.c_int32),
                               P(ctypes.c_int32)]
+    L.dq_solve_noalloc.argtypes = [ctypes.c_int, P(ProblemDesc), P(SolveOpts), P(Outputs), P(Result), vp]
     L.dq_context_profile.argtypes = [vp, ctypes.c_int32]
     L.dq_context_stats.argtypes = [vp, P(Stats), ctypes.c_int32]
     for name in SYMBOLS[:-2]:
