@@ -229,7 +229,8 @@ dq_status dq_autotune(dq_problem *const *probs, int32_t count, const dq_solve_op
  * admitted requests.  dq_submit enqueues a solve of `prob` (which must stay
  * alive until the ticket is polled) with new q/g vectors (host double, NULL
  * keeps the handle's) and warm start from the handle's last lambda; it
- * returns DQ_ERR_REJECTED when the request can never fit the budget.
+ * returns DQ_ERR_REJECTED when the request can never fit the budget or the
+ * loop's per-request limits (FP32 instances with n <= 512, p <= 1024).
  * dq_poll returns DQ_PENDING until the ticket completes, then the result and
  * the outputs (host double).  dq_serve_stop drains and stops the loop. */
 dq_status dq_serve_start(dq_context *ctx, int32_t slots, int64_t hbm_budget_bytes);

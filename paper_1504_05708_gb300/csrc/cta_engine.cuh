@@ -309,17 +309,92 @@ __device__ EvalOut cta_eval(const CtaInst<T>& I, CtaWs<T>& W, const T* u, const 
 // the Rayleigh quotient theta in FP64.  Returns theta + ||A v - theta v||, an
 // upper estimate once v lies in the top eigenspace; stops when the residual
 // is below rtol * theta or after max_it steps.
+// Largest eigenvalue theta of the m x m symmetric tridiagonal matrix with
+// diagonal a and off-diagonal b (b[i] joins rows i and i+1), and |s_m|, the
+// last component of its unit eigenvector.  Run by warp 0 in FP32 (FP64 runs
+// at a small fraction of the FP32 rate on this GPU): multisection on Sturm
+// counts, 32 points per round, then the three-term eigenvector recurrence
+// (rescaled) on lane 0.  af, bf: m-float scratch.  Results in out[0], out[1].
+__device__ inline void warp_tridiag_top(const double* a, const double* b, int m, float* af, float* bf,
+                                        double* out) {
+  const int lane = threadIdx.x & 31;
+  float lo = INFINITY, hi = -INFINITY;
+  for (int i = lane; i < m; i += 32) {
+    af[i] = float(a[i]);
+    bf[i] = i + 1 < m ? float(b[i]) : 0.f;
+    const float r = float((i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0));
+    lo = fminf(lo, af[i] - r);
+    hi = fmaxf(hi, af[i] + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  __syncwarp();
+  for (int round = 0; round < 8; ++round) {
+    const float x = lo + (hi - lo) * (float(lane + 1) / 33.f);
+    int cnt = 0;
+    float d = 1.f;
+    for (int i = 0; i < m; ++i) {
+      d = (af[i] - x) - (i > 0 ? bf[i - 1] * bf[i - 1] / d : 0.f);
+      if (d == 0.f) d = -1e-30f;
+      cnt += d < 0.f;
+    }
+    const unsigned ball = __ballot_sync(0xffffffffu, cnt == m);  // x above every eigenvalue
+    const int first = ball ? __ffs(ball) - 1 : 32;
+    const float nhi = first < 32 ? __shfl_sync(0xffffffffu, x, first) : hi;
+    const float nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0) : lo;
+    lo = nlo;
+    hi = nhi;
+    if (hi - lo <= 1e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+  }
+  if (lane == 0) {
+    float up = 0.f, u = 1.f, nrm2 = 1.f;
+    for (int i = 0; i + 1 < m; ++i) {
+      if (bf[i] == 0.f) {
+        up = 0.f; u = 1.f; nrm2 = 1.f;
+        continue;
+      }
+      const float un = ((hi - af[i]) * u - (i > 0 ? bf[i - 1] * up : 0.f)) / bf[i];
+      up = u;
+      u = un;
+      nrm2 += u * u;
+      if (nrm2 > 1e30f) {
+        const float sc = rsqrtf(nrm2);
+        up *= sc; u *= sc; nrm2 = 1.f;
+      }
+    }
+    out[0] = hi;
+    out[1] = fabsf(u) * rsqrtf(nrm2);
+  }
+}
+
+// lambda_max of Q (which = 0) or G'G (which = 1) by the Lanczos method
+// without reorthogonalisation (only the extreme Ritz value is used).  After
+// step j the largest Ritz value theta of T_j and its residual r = beta_j |s_j|
+// (there is an eigenvalue within r of theta) give the estimate theta + 2 r,
+// accepted once r <= rtol * theta; the factor 2 covers most starts whose
+// component along the top eigenvector is small (Lanczos then settles first on
+// the next eigenvalue).  A 1e-5 relative margin covers the FP32 tridiagonal
+// solve.  Scratch: A.x, B.x, A.Qx, A.Gx, A.xp, A.xn, dn, usum.
 template <typename T>
-__device__ double cta_power(const CtaInst<T>& I, CtaWs<T>& W, int which, int max_it, double rtol) {
+__device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int max_it, int which, double rtol) {
   const int n = I.n, p = I.p;
   T* v = W.A.x;
+  T* vp = W.B.x;
   T* w = W.A.Qx;
   T* t = W.A.Gx;
+  double* al = W.dn;
+  double* be = W.usum;
   const T v0 = T(1.0 / sqrt(double(n)));
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = v0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    v[i] = v0;
+    vp[i] = T(0);
+  }
   __syncthreads();
-  double theta = 0.0, r = 0.0;
-  for (int it = 0; it < max_it; ++it) {
+  const int mmax = min(n, max_it);
+  double theta = 0.0, r = 0.0, beta_prev = 0.0;
+  for (int j = 0; j < mmax; ++j) {
     if (which == 0) {
       mtv<T>(W.Q, n, n, n, v, w);
     } else {
@@ -328,22 +403,42 @@ __device__ double cta_power(const CtaInst<T>& I, CtaWs<T>& W, int which, int max
       mtv<T>(W.G, p, n, n, t, w);
     }
     __syncthreads();
-    double pvw = 0.0, pww = 0.0;
+    double pa = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) pa += double(v[i]) * double(w[i]);
+    const double alpha = block_sum(pa, W.red);
+    double pb = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      pvw += double(v[i]) * double(w[i]);
-      pww += double(w[i]) * double(w[i]);
+      const double rr = double(w[i]) - alpha * double(v[i]) - beta_prev * double(vp[i]);
+      w[i] = T(rr);
+      pb += rr * rr;
     }
-    const double vw = block_sum(pvw, W.red);
-    const double ww = block_sum(pww, W.red);
-    theta = vw;
-    r = sqrt(fmax(ww - vw * vw, 0.0));
-    if (ww == 0.0 || (it >= 3 && r <= rtol * theta)) break;
-    const double inv = 1.0 / sqrt(ww);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = T(double(w[i]) * inv);
+    const double beta = sqrt(block_sum(pb, W.red));
+    if (threadIdx.x == 0) {
+      al[j] = alpha;
+      be[j] = beta;
+    }
+    const bool last = j + 1 == mmax || !(beta > 1e-300);
+    if (last || (j >= 3 && ((j + 1) % 4 == 0))) {
+      __syncthreads();
+      if (threadIdx.x < 32) warp_tridiag_top(al, be, j + 1, (float*)W.A.xp, (float*)W.A.xn, W.red + 34);
+      __syncthreads();
+      theta = W.red[34];
+      r = beta * W.red[35];
+      if (!(beta > 1e-300) || j + 1 == n) {  // invariant subspace: theta is exact up to rounding
+        r = 0.0;
+        break;
+      }
+      if (r <= rtol * theta) break;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      vp[i] = v[i];
+      v[i] = T(double(w[i]) / beta);
+    }
+    beta_prev = beta;
     __syncthreads();
   }
   __syncthreads();
-  return theta + r;
+  return theta + 2.0 * r + 1e-5 * fabs(theta);
 }
 
 __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -408,8 +503,8 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
   }
   __syncthreads();
   // FP64 constants (a1): lambda_max(Q), ||G||^2, then L_L, sigma_L, L_d, rho
-  if (isnan(I.lmax_Q)) I.lmax_Q = cta_power<T>(I, W, 0, 300, 1e-3);
-  if (isnan(I.normG2)) I.normG2 = p > 0 ? cta_power<T>(I, W, 1, 300, 1e-3) : 0.0;
+  if (isnan(I.lmax_Q)) I.lmax_Q = cta_lanczos<T>(I, W, 160, 0, 1e-3);
+  if (isnan(I.normG2)) I.normG2 = p > 0 ? cta_lanczos<T>(I, W, 160, 1, 1e-3) : 0.0;
   const double lmin = isnan(I.lmin_Q) ? 0.0 : I.lmin_Q;
   if (isnan(I.rho)) I.rho = (I.alg == ALG_ADGM || I.alg == ALG_ADFGM) ? (I.normG2 > 0.0 ? 1.0 / I.normG2 : 1.0) : 0.0;
   if (isnan(I.LL)) I.LL = I.lmax_Q + I.rho * I.normG2;

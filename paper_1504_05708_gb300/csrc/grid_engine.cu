@@ -60,7 +60,7 @@ struct Ctrl {          // device control block of the grid engine
   int inner_done;      // set by the certificate kernel
   int k_stop;          // iteration at which the inner loop stopped
   unsigned int arrive; // last-block counter of the reductions
-  int pad;
+  int wait_err;        // set when a bounded wait of the single-pass kernel gave up
   double cert;
   double sums[8];      // results of the reduction kernels
 };
@@ -375,6 +375,84 @@ __global__ void __launch_bounds__(512) k_vw(const T* v, const T* w, int n, doubl
   }
 }
 
+// Lanczos three-term step on the device: w -= alpha v + beta_prev v_prev with
+// alpha = v.w from k_vw (ctrl->sums[4]), and ||w||^2 into ctrl->sums[6].
+template <typename T>
+__global__ void __launch_bounds__(512) k_lz_update(const T* v, const T* vp, T* w, int n, double beta_prev,
+                                                   double* partials, Ctrl* ctrl) {
+  const double alpha = ctrl->sums[4];
+  double part[1] = {0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double r = double(w[i]) - alpha * double(v[i]) - beta_prev * double(vp[i]);
+    w[i] = T(r);
+    part[0] += r * r;
+  }
+  double out[1];
+  if (grid_reduce<1>(part, partials, ctrl, out) && threadIdx.x == 0) ctrl->sums[6] = out[0];
+}
+
+// v_prev = v, v = w / beta (beta = sqrt(ctrl->sums[6])); init: v = 1/sqrt(n), v_prev = 0.
+template <typename T>
+__global__ void k_lz_next(T* v, T* vp, const T* w, int n, const Ctrl* ctrl, int init) {
+  const double nb = ctrl->sums[6];
+  const double inv = nb > 0.0 ? 1.0 / sqrt(nb) : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (init) {
+      v[i] = T(1.0 / sqrt(double(n)));
+      vp[i] = T(0);
+    } else {
+      vp[i] = v[i];
+      v[i] = T(double(w[i]) * inv);
+    }
+  }
+}
+
+// Largest eigenvalue theta of the m x m symmetric tridiagonal matrix with
+// diagonal a and off-diagonal b (b[i] joins rows i and i+1) by bisection on
+// Sturm counts, and |s_m|, the last component of its unit eigenvector, from
+// the three-term recurrence (host, FP64).
+static void tridiag_top(const std::vector<double>& a, const std::vector<double>& b, int m, double* theta,
+                        double* s_last) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto below = [&](double x) {  // number of eigenvalues < x
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+      d = (a[i] - x) - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      cnt += d < 0.0;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::max(fabs(lo), fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) == m) hi = mid; else lo = mid;
+  }
+  *theta = hi;
+  // eigenvector components u_0 = 1, u_{i+1} = ((theta - a_i) u_i - b_{i-1} u_{i-1}) / b_i, rescaled
+  double up = 0.0, u = 1.0, nrm2 = 1.0;
+  for (int i = 0; i + 1 < m; ++i) {
+    if (b[i] == 0.0) {  // the matrix splits: the leading block's vector ends here
+      up = 0.0; u = 1.0; nrm2 = 1.0;
+      continue;
+    }
+    const double un = ((hi - a[i]) * u - (i > 0 ? b[i - 1] * up : 0.0)) / b[i];
+    up = u;
+    u = un;
+    nrm2 += u * u;
+    if (nrm2 > 1e200) {
+      const double sc = 1.0 / sqrt(nrm2);
+      up *= sc; u *= sc; nrm2 = 1.0;
+    }
+  }
+  *s_last = fabs(u) / sqrt(nrm2);
+}
+
 template <typename T>
 __global__ void k_scale(const T* w, T* v, int n, const Ctrl* ctrl, T fill) {
   const double ww = ctrl->sums[5];
@@ -530,15 +608,26 @@ struct GridRun {
     return rows<true>(J);
   }
 
-  // lambda_max of Q (which = 0) or G'G (which = 1) by power iteration.
+  // lambda_max of Q (which = 0) or G'G (which = 1) by the Lanczos method
+  // (no reorthogonalisation: only the extreme Ritz value is used): after step
+  // j the largest Ritz value theta of the tridiagonal T_j and its residual
+  // r = beta_j |s_j| (there is an eigenvalue within r of theta) give the
+  // estimate theta + 2 r, accepted once r <= 1e-3 theta; the factor 2 covers
+  // most starts with a small component along the top eigenvector.  Matrix
+  // products run on the device; the tridiagonal problem (at most 200 x 200)
+  // on the host.
   dq_status power(int which, double* out) {
     T* vv = v(W->pv);
     T* ww = v(W->pw);
     T* tt = v(W->pt);
+    T* vp = v(W->XB[0]);  // scratch here: the last-iterate chain is idle during constants
     const int eb = std::min(blocks, 4096);
-    k_scale<T><<<eb, 256, 0, st>>>(ww, vv, n, W->ctrl, T(1.0 / sqrt(double(n))));
-    double theta = 0.0, r = 0.0;
-    for (int it = 0; it < 300; ++it) {
+    k_lz_next<T><<<eb, 256, 0, st>>>(vv, vp, ww, n, W->ctrl, 1);
+    ++P->ctx->launches;
+    std::vector<double> al, be;
+    double theta = 0.0, r = 0.0, beta_prev = 0.0;
+    const int mmax = std::min(n, 200);
+    for (int j = 0; j < mmax; ++j) {
       cudaError_t e;
       if (which == 0) {
         e = gemv(Q(), n, nullptr, 0, n, vv, ww, nullptr);
@@ -547,20 +636,31 @@ struct GridRun {
         if (e == cudaSuccess) e = gemv(GT(), n, nullptr, 0, p, tt, ww, nullptr);
       }
       if (e != cudaSuccess) {
-        set_error("power iteration launch: %s", cudaGetErrorString(e));
+        set_error("Lanczos product launch: %s", cudaGetErrorString(e));
         return DQ_ERR_CUDA;
       }
       k_vw<T><<<eb, 512, 0, st>>>(vv, ww, n, W->partials, W->ctrl);
-      P->ctx->launches += 2;  // k_vw and the k_scale before it
+      k_lz_update<T><<<eb, 512, 0, st>>>(vv, vp, ww, n, beta_prev, W->partials, W->ctrl);
+      P->ctx->launches += 2;
       DQ_CK(cudaMemcpyAsync(W->hctrl, W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       DQ_CK(cudaStreamSynchronize(st));
-      const double vw = W->hctrl->sums[4], ww2 = W->hctrl->sums[5];
-      theta = vw;
-      r = sqrt(std::max(ww2 - vw * vw, 0.0));
-      if (ww2 == 0.0 || (it >= 3 && r <= 1e-3 * theta)) break;
-      k_scale<T><<<eb, 256, 0, st>>>(ww, vv, n, W->ctrl, T(0));
+      const double alpha = W->hctrl->sums[4], beta = sqrt(std::max(W->hctrl->sums[6], 0.0));
+      al.push_back(alpha);
+      be.push_back(beta);
+      double sl = 0.0;
+      tridiag_top(al, be, j + 1, &theta, &sl);
+      r = beta * sl;
+      if (!(beta > 1e-300) || j + 1 == n) {  // invariant subspace: theta is exact
+        r = 0.0;
+        break;
+      }
+      if (j >= 2 && r <= 1e-3 * theta) break;
+      k_lz_next<T><<<eb, 256, 0, st>>>(vv, vp, ww, n, W->ctrl, 0);
+      ++P->ctx->launches;
+      DQ_CK(cudaGetLastError());
+      beta_prev = beta;
     }
-    *out = theta + r;
+    *out = theta + 2.0 * r + 1e-12 * fabs(theta);
     return DQ_OK;
   }
 
@@ -618,15 +718,20 @@ struct GridRun {
     DQ_CK(cudaMemcpyAsync(W->rows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, st));
     v2_nQ = nQ;
     v2_nG = nG;
-    v2_npt = std::max(2, ((n4 + V2_THREADS - 1) / V2_THREADS + 1) / 2 * 2);
+    v2_npt = std::max(2, ((n4 + V2_CONS - 1) / V2_CONS + 1) / 2 * 2);
     (void)maxq;  // Q rows are dealt round-robin: each Q-CTA holds x_i of ceil(n / nQ) rows
-    v2_smem = 2 * (size_t)n4 * 16 + ((size_t)(n + nQ - 1) / nQ + 1) * 4 + 256;
+    const size_t xs_len = std::max<size_t>((n + nQ - 1) / nQ, nG > 0 ? (size_t)(p + nG - 1) / nG : 0) + 1;
+    v2_smem = (size_t)V2_STAGES * V2_CH4 * 16 + xs_len * 4 + 256;
     return DQ_OK;
   }
 
   cudaError_t v2_pass(const V2Args& A) {
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern) {
+      if (v2_smem > max_dynamic_smem((const void*)kern, P->ctx->smem_optin)) {
+        e = cudaErrorInvalidValue;
+        return;
+      }
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v2_smem);
       if (e == cudaSuccess) {
         kern<<<v2_nQ + v2_nG, V2_THREADS, v2_smem, st>>>(A);
@@ -638,8 +743,7 @@ struct GridRun {
       case 4: go(k_v2_pass<4>); break;
       case 6: go(k_v2_pass<6>); break;
       case 8: go(k_v2_pass<8>); break;
-      case 10: go(k_v2_pass<10>); break;
-      default: go(k_v2_pass<12>); break;
+      default: go(k_v2_pass<10>); break;
     }
     ++P->ctx->launches;
     return e;
@@ -741,6 +845,7 @@ struct GridRun {
             A.gx1 = v(GX[sx]); A.mu = mu; A.g = g();
             A.beta_prev = (float)beta; A.beta_next = (float)bnext; A.L = (float)LL; A.rho = (float)rho; A.cone = cone;
             A.xout = v(X[sn]); A.gxout = v(GX[sn]); A.dotQ = W->dotQ; A.partials = W->parts; A.done = dn;
+            A.err = &W->ctrl->wait_err;
             const double bytes = 4.0 * (double(W->hoff[n]) + (aug ? double(p) * n : 0.0) + 10.0 * n + (aug ? 4.0 * p : 0));
             if (P->ctx->profile) {
               while ((int)W->evpool.size() < evn + 2) {
@@ -757,8 +862,8 @@ struct GridRun {
               e = v2_pass(A);
             }
             if (e != cudaSuccess) break;
-            k_v2_reduce<<<P->ctx->num_sms * 2, 256, 0, st>>>(W->parts, v2_nQ, v2_nG, n / 4, W->dotQ, v(QX[sn]),
-                                                             aug ? v(W->tn) : nullptr, dn);
+            k_v2_reduce<<<(n / 4 + V2R_COLS - 1) / V2R_COLS, V2R_COLS * V2R_GROUPS, 0, st>>>(
+                W->parts, v2_nQ, v2_nG, n / 4, W->dotQ, v(QX[sn]), aug ? v(W->tn) : nullptr, dn);
             ++P->ctx->launches;
             if ((e = cudaGetLastError()) != cudaSuccess) break;
             beta = bnext;
@@ -818,12 +923,16 @@ struct GridRun {
       return DQ_ERR_CUDA;
     }
     DQ_CK(cudaStreamSynchronize(st));
-    if (fixed > 0) {
+    if (fixed > 0 && !use_v2) {
       kstop = k;
     } else {
       DQ_CK(cudaMemcpyAsync(W->hctrl, W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
       DQ_CK(cudaStreamSynchronize(st));
-      kstop = W->hctrl->inner_done ? W->hctrl->k_stop : k;
+      kstop = fixed > 0 ? k : (W->hctrl->inner_done ? W->hctrl->k_stop : k);
+      if (W->hctrl->wait_err) {
+        set_error("single-pass iteration: a bounded shared-memory pipeline wait gave up");
+        return DQ_ERR_TIMEOUT;
+      }
     }
     inner_total += kstop;
     *slot = slot_of(kstop);
@@ -1046,7 +1155,7 @@ static dq_status solve_T(dq_problem* P, GridWs* W, const SolveCfg& c, const dq_o
   if constexpr (std::is_same<T, float>::value) {
     // the single-pass iteration runs when DQ_GRID_SINGLE_PASS=1 and the rows fit its layout
     const char* ev = getenv("DQ_GRID_SINGLE_PASS");
-    R.use_v2 = (P->n % 4 == 0) && (P->n / 4 <= V2_THREADS * 12) && (ev && ev[0] == '1');
+    R.use_v2 = (P->n % 4 == 0) && (P->n / 4 <= V2_CONS * 10) && (ev && ev[0] == '1');
   }
   return R.solve(out, res);
 }

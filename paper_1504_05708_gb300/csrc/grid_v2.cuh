@@ -9,14 +9,21 @@
 //   * G is read once per iteration: row j's dot r_j = G_j x^k gives G x^k
 //     (carried for the dual gradient) and, by linearity of G y in the
 //     x-side form, w_j = [mu_j + rho (G y^{k+1} + g)_j]_+ of the next
-//     iteration, so the same row (held in shared memory) adds w_j G_j to
-//     G' w of the next iteration.  Rows arrive by double-buffered bulk copies.
-// A CTA is either a Q-CTA (a contiguous range of packed rows with about the
-// same element count as every other CTA) or a G-CTA (a range of G rows).
-// Each keeps its column partial sums for the 512 threads' own columns in
-// registers and writes one partial vector; k_v2_reduce adds the partial
-// vectors in CTA order (deterministic) and the row dots.  HBM bytes per
-// iteration: 4 (n(n+1)/2 + p n) instead of 4 (n^2 + 2 p n).
+//     iteration, so the same row (still in shared memory) adds w_j G_j to
+//     G' w of the next iteration.
+// A CTA is either a Q-CTA (rows c, c + nQ, c + 2 nQ, ...: every Q-CTA gets
+// the same mix of long and short rows) or a G-CTA (a contiguous range of G
+// rows).  Rows stream through a ring of 16 KB shared-memory stages filled by
+// bulk copies (full/empty mbarrier pairs): thread 0 fills the ring at the
+// start, and refills a stage as soon as all 16 warps have released it, so up
+// to 192 KB per SM are in flight.  (A separate producer warp would make 17
+// warps per CTA and cut the register budget from 128 to 96 per thread.)  A
+// chunk covers 1024 float4 columns at a fixed global position, which is two
+// of each consumer thread's register-resident column slots (t + 512 m): the
+// iterate x^k and the column partial sums never leave registers.  Each CTA
+// writes one partial vector; k_v2_reduce adds the partial vectors in a fixed
+// order (deterministic) and the row dots.  HBM bytes per iteration:
+// 4 (n(n+1)/2 + p n) instead of 4 (n^2 + 2 p n).
 #pragma once
 #include "dq_common.cuh"
 #include "tc_common.cuh"
@@ -26,7 +33,7 @@ namespace dq {
 struct V2Args {
   int n, p, n4;                       // n4 = n / 4 (n a multiple of 4)
   int nQ, nG;
-  const int* qrow;                    // nQ + 1 row bounds of the Q-CTAs
+  const int* qrow;                    // unused (Q rows are dealt round-robin)
   const int* grow;                    // nG + 1 row bounds of the G-CTAs
   const long long* qoff;              // n packed-row offsets (floats, multiples of 4)
   const float* Qp;                    // packed upper triangle
@@ -43,28 +50,103 @@ struct V2Args {
   float* dotQ;                        // row dots of the packed rows
   float4* partials;                   // (nQ + nG) x n4
   const int* done;
+  int* err;                           // set to 1 when a bounded wait gave up
 };
 
-static constexpr int V2_THREADS = 512;
-static constexpr int V2_RB = 64;  // rows between flushes of the row-dot partials
+static constexpr int V2_CONS = 512;                 // threads (16 warps), all consumers
+static constexpr int V2_THREADS = V2_CONS;
+static constexpr int V2_CH4 = 2 * V2_CONS;          // float4 per chunk (16 KB)
+static constexpr int V2_STAGES = 12;                // ring depth (192 KB)
+static constexpr int V2_RB = 64;                    // rows between flushes of the row dots
+static constexpr unsigned long long V2_WAIT_NS = 2000000000ull;
 
+__device__ __forceinline__ void v2_consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(V2_CONS) : "memory"); }
+
+// Warp sum (butterfly, every lane gets the total).  Each lane's value is
+// already a compensated partial over its columns; the five pairwise levels
+// add at most 5 roundings.
+__device__ __forceinline__ float v2_warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// NPT (even) register slots of float4 columns per consumer thread; a row spans
+// at most NPT / 2 <= V2_STAGES chunks.
 template <int NPT>
 __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
+  static_assert(NPT % 2 == 0 && NPT / 2 <= V2_STAGES, "chunk ring too shallow");
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ __align__(8) uint64_t full[2];
-  __shared__ float sdot[V2_RB][V2_THREADS / 32];
-  __shared__ double sred[V2_THREADS / 32 + 1];
+  __shared__ __align__(8) uint64_t full[V2_STAGES], empty[V2_STAGES];
+  __shared__ float sdot[V2_RB][V2_CONS / 32];
+  __shared__ float sred[2][V2_CONS / 32];
   if (a.done && *(volatile const int*)a.done) return;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool qcta = blockIdx.x < a.nQ;
-  // prologue: x^k = [y - grad(y)/L]_U for this thread's columns (float4 units t + 512 m)
+  const int c = blockIdx.x, nQ = a.nQ, n4 = a.n4;
+  const int kl = (n4 - 1) / V2_CH4;  // last chunk of every row
+  const int cnt = qcta ? (c < a.n ? (a.n - 1 - c) / nQ + 1 : 0) : 0;
+  const int j0 = qcta ? 0 : a.grow[c - nQ], j1 = qcta ? 0 : a.grow[c - nQ + 1];
+  float4* ring = (float4*)sm;
+  // Q-CTA: x_i of its rows; G-CTA: per-row constant of w (see the G branch)
+  float* xs = (float*)(sm + (size_t)V2_STAGES * V2_CH4 * 16);
+  if (t == 0) {
+    for (int s = 0; s < V2_STAGES; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], V2_CONS / 32);
+    }
+    tc::mbar_init_fence();
+  }
+  __syncthreads();
+
+  // Issue cursor (used by thread 0 only): chunk pk of this CTA's pr-th row;
+  // chunk number pg (position in the CTA's sequence) goes to stage pg % STAGES.
+  const int rows = qcta ? cnt : j1 - j0;
+  int pr = 0, pk = 0;
+  uint32_t pg = 0;
+  bool ok = true;
+  auto row_of = [&](int r) { return qcta ? c + r * nQ : j0 + r; };
+  auto first_chunk = [&](int r) { return qcta ? (row_of(r) >> 2) / V2_CH4 : 0; };
+  auto issue_next = [&]() {  // thread 0: copy the cursor's chunk into stage pg % STAGES, advance
+    const int i = row_of(pr);
+    const int f0 = qcta ? (i >> 2) : 0;
+    const float* src = qcta ? a.Qp + a.qoff[i] + 4ll * (max(pk * V2_CH4, f0) - f0)
+                            : a.G + (size_t)i * a.n + 4ll * (pk * V2_CH4);
+    const int b4 = max(pk * V2_CH4, f0), e4 = min((pk + 1) * V2_CH4, n4);
+    const uint32_t bytes = (uint32_t)(e4 - b4) * 16u;
+    const int s = (int)(pg % V2_STAGES);
+    tc::mbar_expect_tx(&full[s], bytes);
+    tc::bulk_g2s(ring + (size_t)s * V2_CH4 + (b4 - pk * V2_CH4), src, bytes, &full[s]);
+    ++pg;
+    if (++pk > kl) {
+      ++pr;
+      if (pr < rows) pk = first_chunk(pr);
+    }
+  };
+  if (t == 0 && rows > 0) {
+    pk = first_chunk(0);
+    for (int s = 0; s < V2_STAGES && pr < rows; ++s) issue_next();
+  }
+  // Release chunk gc (every warp, after its last read of the stage); thread 0
+  // then waits for all 16 releases and refills the stage with the next chunk.
+  auto release = [&](uint32_t gc) {
+    const int s = (int)(gc % V2_STAGES);
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(&empty[s]);
+    if (t == 0 && pr < rows) {
+      ok = tc::mbar_wait(&empty[s], (gc / V2_STAGES) & 1, V2_WAIT_NS) && ok;
+      issue_next();
+    }
+  };
+
+  // ---------------- consumers: prologue x^k = [y - grad(y)/L]_U for this thread's columns
   float4 xr[NPT];
   const float b = a.beta_prev;
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
-    const int c4 = t + V2_THREADS * m;
+    const int c4 = t + V2_CONS * m;
     float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (c4 < a.n4) {
+    if (c4 < n4) {
       const float4 x1 = ((const float4*)a.x1)[c4], x2 = ((const float4*)a.x2)[c4];
       const float4 q1 = ((const float4*)a.qx1)[c4], q2 = ((const float4*)a.qx2)[c4];
       const float4 ad = ((const float4*)a.addv)[c4];
@@ -81,27 +163,10 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
       o.z = step(x1.z, x2.z, q1.z, q2.z, ad.z, tw.z, lo.z, hi.z);
       o.w = step(x1.w, x2.w, q1.w, q2.w, ad.w, tw.w, lo.w, hi.w);
       // every CTA computes x^k; CTA c stores the c-th slice
-      const int per = (a.n4 + gridDim.x - 1) / gridDim.x;
-      if (c4 >= blockIdx.x * per && c4 < (blockIdx.x + 1) * per) ((float4*)a.xout)[c4] = o;
-    }
-    xr[m] = o;
-  }
-  float4 part[NPT];
-#pragma unroll
-  for (int m = 0; m < NPT; ++m) part[m] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-  if (qcta) {
-    // rows c, c + nQ, c + 2 nQ, ... (every CTA gets the same mix of long and
-    // short rows), streamed through a double buffer of bulk copies
-    const int c = blockIdx.x, nQ = a.nQ;
-    const int cnt = c < a.n ? (a.n - 1 - c) / nQ + 1 : 0;
-    float* xs = (float*)(sm + 2 * (size_t)a.n4 * 16);  // x_i of this CTA's rows
-    auto qbuf = [&](int s) { return (const float4*)(sm + (size_t)s * a.n4 * 16); };
-#pragma unroll
-    for (int m = 0; m < NPT; ++m) {
-      const int c4 = t + V2_THREADS * m;
-      if (c4 < a.n4) {
-        const float xv[4] = {xr[m].x, xr[m].y, xr[m].z, xr[m].w};
+      const int per = (n4 + gridDim.x - 1) / gridDim.x;
+      if (c4 >= c * per && c4 < (c + 1) * per) ((float4*)a.xout)[c4] = o;
+      if (qcta) {
+        const float xv[4] = {o.x, o.y, o.z, o.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = 4 * c4 + u;
@@ -109,165 +174,193 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
         }
       }
     }
-    if (t == 0) {
-      tc::mbar_init(&full[0], 1);
-      tc::mbar_init(&full[1], 1);
-      tc::mbar_init_fence();
-    }
-    __syncthreads();
-    auto issue = [&](int idx, int s) {
-      const int i = c + idx * nQ;
-      const uint32_t bytes = (uint32_t)(a.n - (i & ~3)) * 4u;
-      tc::mbar_expect_tx(&full[s], bytes);
-      tc::bulk_g2s((void*)qbuf(s), a.Qp + a.qoff[i], bytes, &full[s]);
-    };
-    if (t == 0)
-      for (int s = 0; s < 2 && s < cnt; ++s) issue(s, s);
+    xr[m] = o;
+  }
+  float4 part[NPT];
+#pragma unroll
+  for (int m = 0; m < NPT; ++m) part[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!qcta) {
+    // w_j = [mu_j + rho (G y^{k+1} + g)_j]_+ with G y^{k+1} = (1 + beta) r_j - beta (G x^{k-1})_j,
+    // r_j = (G x^k)_j: w_j = [A_j + rho (1 + beta) r_j]_+, A_j = mu_j + rho (g_j - beta (G x^{k-1})_j)
+    for (int j = j0 + t; j < j1; j += V2_CONS) xs[j - j0] = a.mu[j] + a.rho * (a.g[j] - a.beta_next * a.gx1[j]);
+  }
+  v2_consumer_sync();  // xs complete
+
+  uint32_t gc = 0;
+  if (qcta) {
     for (int rb = 0; rb < cnt; rb += V2_RB) {
       const int re = min(cnt, rb + V2_RB);
       for (int idx = rb; idx < re; ++idx) {
         const int i = c + idx * nQ;
-        const int s = idx & 1;
-        tc::mbar_wait(&full[s], (idx >> 1) & 1, 2000000000ull);
-        const float4* row = qbuf(s);
-        const int f0 = i >> 2;  // first float4 column of the packed row
+        const int f0 = i >> 2, kf = f0 / V2_CH4;
         const float xi = xs[idx];
         float sa = 0.f, comp = 0.f;
 #pragma unroll
-        for (int m = 0; m < NPT; ++m) {
-          const int c4 = t + V2_THREADS * m;
-          if (c4 >= f0 && c4 < a.n4) {
-            const float4 v = row[c4 - f0];
-            float d = v.x * xr[m].x;
-            d = fmaf(v.y, xr[m].y, d);
-            d = fmaf(v.z, xr[m].z, d);
-            d = fmaf(v.w, xr[m].w, d);
-            const float yk = d - comp, tk = sa + yk;  // Kahan pair
-            comp = (tk - sa) - yk;
-            sa = tk;
-            part[m].x = fmaf(xi, v.x, part[m].x);
-            part[m].y = fmaf(xi, v.y, part[m].y);
-            part[m].z = fmaf(xi, v.z, part[m].z);
-            part[m].w = fmaf(xi, v.w, part[m].w);
+        for (int k = 0; k < NPT / 2; ++k) {
+          if (k >= kf && k <= kl) {  // the same for every thread of the CTA
+            const int s = (int)(gc % V2_STAGES);
+            ok = tc::mbar_wait(&full[s], (gc / V2_STAGES) & 1, V2_WAIT_NS) && ok;
+            const float4* ch = ring + (size_t)s * V2_CH4;  // column c4 at ch[c4 - k * V2_CH4]
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int m = 2 * k + h, c4 = t + V2_CONS * m;
+              if (c4 >= f0 && c4 < n4) {
+                const float4 v = ch[c4 - k * V2_CH4];
+                float d = v.x * xr[m].x;
+                d = fmaf(v.y, xr[m].y, d);
+                d = fmaf(v.z, xr[m].z, d);
+                d = fmaf(v.w, xr[m].w, d);
+                const float yk = d - comp, tk = sa + yk;  // Kahan pair
+                comp = (tk - sa) - yk;
+                sa = tk;
+                part[m].x = fmaf(xi, v.x, part[m].x);
+                part[m].y = fmaf(xi, v.y, part[m].y);
+                part[m].z = fmaf(xi, v.z, part[m].z);
+                part[m].w = fmaf(xi, v.w, part[m].w);
+              }
+            }
+            release(gc);
+            ++gc;
           }
         }
-        double tot = double(sa) - double(comp);
-        for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-        if (lane == 0) sdot[idx - rb][warp] = float(tot);
-        __syncthreads();  // buffer s free again
-        if (t == 0 && idx + 2 < cnt) issue(idx + 2, s);
+        const float tot = v2_warp_sum(sa - comp);
+        if (lane == 0) sdot[idx - rb][warp] = tot;
       }
+      v2_consumer_sync();
       if (t < re - rb) {
-        double s = 0.0;
-        for (int w = 0; w < V2_THREADS / 32; ++w) s += sdot[t][w];
-        a.dotQ[c + (rb + t) * nQ] = float(s);
+        float sh = 0.f, sl = 0.f;  // compensated (TwoSum) sum of the 16 warp sums
+        for (int w = 0; w < V2_CONS / 32; ++w) {
+          const float b2 = sdot[t][w], s2 = sh + b2, bb = s2 - sh;
+          sl += (sh - (s2 - bb)) + (b2 - bb);
+          sh = s2;
+        }
+        a.dotQ[c + (rb + t) * nQ] = sh + sl;
       }
-      __syncthreads();
+      v2_consumer_sync();
     }
   } else {
-    // G rows through a double buffer of bulk copies
-    const int gi = blockIdx.x - a.nQ;
-    const int j0 = a.grow[gi], j1 = a.grow[gi + 1];
-    auto buf = [&](int s) { return (float4*)(sm + (size_t)s * a.n4 * 16); };
-    const uint32_t rowb = (uint32_t)a.n4 * 16;
-    if (t == 0) {
-      tc::mbar_init(&full[0], 1);
-      tc::mbar_init(&full[1], 1);
-      tc::mbar_init_fence();
-    }
-    __syncthreads();
-    if (t == 0) {
-      for (int s = 0; s < 2 && j0 + s < j1; ++s) {
-        tc::mbar_expect_tx(&full[s], rowb);
-        tc::bulk_g2s(buf(s), a.G + (size_t)(j0 + s) * a.n, rowb, &full[s]);
-      }
-    }
-    bool ok = true;
     for (int j = j0; j < j1; ++j) {
-      const int s = (j - j0) & 1;
-      const uint32_t ph = ((j - j0) >> 1) & 1;
-      ok = ok && tc::mbar_wait(&full[s], ph, 2000000000ull);
-      float sacc = 0.f, comp = 0.f;
+      const uint32_t g0 = gc;
+      float sa = 0.f, comp = 0.f;
 #pragma unroll
-      for (int m = 0; m < NPT; ++m) {
-        const int c4 = t + V2_THREADS * m;
-        if (c4 < a.n4) {
-          const float4 v = buf(s)[c4];
-          float d = v.x * xr[m].x;
-          d = fmaf(v.y, xr[m].y, d);
-          d = fmaf(v.z, xr[m].z, d);
-          d = fmaf(v.w, xr[m].w, d);
-          const float yk = d - comp, tk = sacc + yk;
-          comp = (tk - sacc) - yk;
-          sacc = tk;
+      for (int k = 0; k < NPT / 2; ++k) {
+        if (k <= kl) {
+          const uint32_t gk = g0 + k;
+          const int s = (int)(gk % V2_STAGES);
+          ok = tc::mbar_wait(&full[s], (gk / V2_STAGES) & 1, V2_WAIT_NS) && ok;
+          const float4* ch = ring + (size_t)s * V2_CH4;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int m = 2 * k + h, c4 = t + V2_CONS * m;
+            if (c4 < n4) {
+              const float4 v = ch[c4 - k * V2_CH4];
+              float d = v.x * xr[m].x;
+              d = fmaf(v.y, xr[m].y, d);
+              d = fmaf(v.z, xr[m].z, d);
+              d = fmaf(v.w, xr[m].w, d);
+              const float yk = d - comp, tk = sa + yk;
+              comp = (tk - sa) - yk;
+              sa = tk;
+            }
+          }
         }
       }
-      double tot = double(sacc) - double(comp);
-      for (int o = 16; o > 0; o >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, o);
-      if (lane == 0) sred[warp] = tot;
-      __syncthreads();
-      if (t == 0) {
-        double r = 0.0;
-        for (int w = 0; w < V2_THREADS / 32; ++w) r += sred[w];
-        sred[V2_THREADS / 32] = r;
-      }
-      __syncthreads();
-      const float r = float(sred[V2_THREADS / 32]);
-      // G x^k, and w of the next iteration from G y^{k+1} = G x^k + beta (G x^k - G x^{k-1})
-      const float gx1 = a.gx1[j];
-      const float gy = r + a.beta_next * (r - gx1);
-      const float v = a.mu[j] + a.rho * (gy + a.g[j]);
-      const float w = a.cone == CONE_EQ ? v : (v > 0.f ? v : 0.f);
-      if (t == 0) a.gxout[j] = r;
+      // one barrier per row: the 16 warp sums go to a buffer that alternates
+      // with the row parity (a warp can only write the next row's buffer
+      // after every warp has passed this row's barrier), and every warp adds
+      // them itself (same order in every warp) to get r_j and w_j
+      const float tot = v2_warp_sum(sa - comp);
+      float* sr = sred[(j - j0) & 1];
+      if (lane == 0) sr[warp] = tot;
+      v2_consumer_sync();
+      const float rf = v2_warp_sum(lane < V2_CONS / 32 ? sr[lane] : 0.f);
+      // G x^k, and w of the next iteration (constant A_j precomputed in xs)
+      const float wv = xs[j - j0] + a.rho * (1.f + a.beta_next) * rf;
+      const float w = a.cone == CONE_EQ ? wv : (wv > 0.f ? wv : 0.f);
+      if (t == 0) a.gxout[j] = rf;
 #pragma unroll
-      for (int m = 0; m < NPT; ++m) {
-        const int c4 = t + V2_THREADS * m;
-        if (c4 < a.n4) {
-          const float4 gv = buf(s)[c4];
-          part[m].x = fmaf(w, gv.x, part[m].x);
-          part[m].y = fmaf(w, gv.y, part[m].y);
-          part[m].z = fmaf(w, gv.z, part[m].z);
-          part[m].w = fmaf(w, gv.w, part[m].w);
+      for (int k = 0; k < NPT / 2; ++k) {
+        if (k <= kl) {
+          const int s = (int)((g0 + k) % V2_STAGES);
+          const float4* ch = ring + (size_t)s * V2_CH4;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int m = 2 * k + h, c4 = t + V2_CONS * m;
+            if (c4 < n4) {
+              const float4 gv = ch[c4 - k * V2_CH4];
+              part[m].x = fmaf(w, gv.x, part[m].x);
+              part[m].y = fmaf(w, gv.y, part[m].y);
+              part[m].z = fmaf(w, gv.z, part[m].z);
+              part[m].w = fmaf(w, gv.w, part[m].w);
+            }
+          }
+          release(g0 + k);
         }
       }
-      __syncthreads();  // buffer s free again
-      if (t == 0 && j + 2 < j1) {
-        tc::mbar_expect_tx(&full[s], rowb);
-        tc::bulk_g2s(buf(s), a.G + (size_t)(j + 2) * a.n, rowb, &full[s]);
-      }
+      gc = g0 + kl + 1;
     }
-    (void)ok;
   }
-  float4* out = a.partials + (size_t)blockIdx.x * a.n4;
+  if (!ok && a.err && lane == 0) atomicExch(a.err, 1);
+  float4* out = a.partials + (size_t)c * n4;
 #pragma unroll
   for (int m = 0; m < NPT; ++m) {
-    const int c4 = t + V2_THREADS * m;
-    if (c4 < a.n4) out[c4] = part[m];
+    const int c4 = t + V2_CONS * m;
+    if (c4 < n4) out[c4] = part[m];
   }
 }
 
 // Q x^k = row dots + column partials of the Q-CTAs; G' w(y^{k+1}) = column
-// partials of the G-CTAs.  Partials are added in CTA order in FP64.
-__global__ void k_v2_reduce(const float4* __restrict__ partials, int nQ, int nG, int n4,
-                            const float* __restrict__ dotQ, float* __restrict__ qxout, float* __restrict__ tnout,
-                            const int* done) {
+// partials of the G-CTAs.  A block owns 32 float4 columns; its 8 thread groups
+// take the partial vectors c = gi, gi + 8, ... (Kahan sums in FP32), and the
+// 8 group sums are added in group order: deterministic for a fixed grid split.
+static constexpr int V2R_COLS = 32, V2R_GROUPS = 8;
+
+__device__ __forceinline__ void v2r_kahan(float4& s, float4& e, const float4 v) {
+  auto one = [](float& sv, float& ev, float x) {
+    const float y = x - ev, tk = sv + y;
+    ev = (tk - sv) - y;
+    sv = tk;
+  };
+  one(s.x, e.x, v.x);
+  one(s.y, e.y, v.y);
+  one(s.z, e.z, v.z);
+  one(s.w, e.w, v.w);
+}
+
+__global__ void __launch_bounds__(V2R_COLS* V2R_GROUPS) k_v2_reduce(const float4* __restrict__ partials, int nQ,
+                                                                     int nG, int n4, const float* __restrict__ dotQ,
+                                                                     float* __restrict__ qxout,
+                                                                     float* __restrict__ tnout, const int* done) {
+  __shared__ float4 sh[2][V2R_GROUPS][V2R_COLS];
   if (done && *(volatile const int*)done) return;
-  for (int c4 = blockIdx.x * blockDim.x + threadIdx.x; c4 < n4; c4 += gridDim.x * blockDim.x) {
-    double q0 = 0, q1 = 0, q2 = 0, q3 = 0;
-    for (int c = 0; c < nQ; ++c) {
-      const float4 v = partials[(size_t)c * n4 + c4];
-      q0 += v.x; q1 += v.y; q2 += v.z; q3 += v.w;
-    }
-    const float4 d = ((const float4*)dotQ)[c4];
-    ((float4*)qxout)[c4] = make_float4(float(q0 + d.x), float(q1 + d.y), float(q2 + d.z), float(q3 + d.w));
-    if (tnout) {
-      double w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-      for (int c = nQ; c < nQ + nG; ++c) {
-        const float4 v = partials[(size_t)c * n4 + c4];
-        w0 += v.x; w1 += v.y; w2 += v.z; w3 += v.w;
+  const int col = threadIdx.x % V2R_COLS, gi = threadIdx.x / V2R_COLS;
+  const int c4 = blockIdx.x * V2R_COLS + col;
+  const bool in = c4 < n4;
+  for (int which = 0; which < (tnout ? 2 : 1); ++which) {
+    const int c0 = which == 0 ? 0 : nQ, c1 = which == 0 ? nQ : nQ + nG;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f), e = s;
+    if (in)
+      for (int cc = c0 + gi; cc < c1; cc += V2R_GROUPS) v2r_kahan(s, e, partials[(size_t)cc * n4 + c4]);
+    sh[0][gi][col] = s;
+    sh[1][gi][col] = make_float4(-e.x, -e.y, -e.z, -e.w);
+    __syncthreads();
+    if (gi == 0 && in) {
+      double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+      for (int q = 0; q < V2R_GROUPS; ++q) {
+        const float4 h = sh[0][q][col], l = sh[1][q][col];
+        r0 += double(h.x) + double(l.x);
+        r1 += double(h.y) + double(l.y);
+        r2 += double(h.z) + double(l.z);
+        r3 += double(h.w) + double(l.w);
       }
-      ((float4*)tnout)[c4] = make_float4(float(w0), float(w1), float(w2), float(w3));
+      if (which == 0) {
+        const float4 d = ((const float4*)dotQ)[c4];
+        ((float4*)qxout)[c4] = make_float4(float(r0 + d.x), float(r1 + d.y), float(r2 + d.z), float(r3 + d.w));
+      } else {
+        ((float4*)tnout)[c4] = make_float4(float(r0), float(r1), float(r2), float(r3));
+      }
     }
+    __syncthreads();
   }
 }
 

@@ -358,7 +358,7 @@ dq_status dq_serve_start(dq_context* ctx, int32_t slots, int64_t hbm_budget_byte
   S->ctx = ctx;
   S->R = slots;
   S->nmax = 512;
-  S->pmax = 512;
+  S->pmax = 1024;
   S->budget = hbm_budget_bytes;
   auto fail = [&](const char* what) {
     cudaGetLastError();

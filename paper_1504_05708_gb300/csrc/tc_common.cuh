@@ -47,11 +47,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait on an mbarrier phase; false when max_ns elapsed first.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long max_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   while (!mbar_try_wait(bar, parity)) {
     if (gtimer() - t0 > max_ns) return false;
   }
   return true;
+}
+
+// Plain arrival (count 1) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
 
 // ------------------------------------------------------- bulk copy (TMA engine)
