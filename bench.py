@@ -228,6 +228,8 @@ def run_gpu(args):
 
     peaks, kind = load_peaks()
     achieved = st["gemv_bytes"] / (st["gemv_ms"] / 1e3) / 1e9 if st["gemv_ms"] > 0 else None
+    # the library takes the single-pass iteration for n % 4 == 0, n <= 20480 unless DQ_GRID_SINGLE_PASS=0
+    single_pass = n % 4 == 0 and n <= 20480 and os.environ.get("DQ_GRID_SINGLE_PASS", "1") != "0"
     r0 = results[-1]
     inner = statistics.mean(r.inner_iters for r in results)
     line = {
@@ -237,13 +239,15 @@ def run_gpu(args):
         "config": {"workload": wl.name, "n": n, "p": p, "alg": wl.alg, "eps": wl.eps,
                    "eps_in": wl.eps_in, "outputs": "last+average", "check_every": wl.check_every,
                    "inner_check_every": wl.inner_check_every,
-                   "l2": "inputs larger than L2 (Q 1.6 GB, G 0.8 GB, G' 0.8 GB)",
+                   "l2": "inputs larger than L2 (packed Q 0.8 GB, G 0.8 GB per inner iteration)",
                    "parallelism": f"replicas{world}"},
         "solve": {"status": r0.status, "outer_iters": r0.outer_iters, "inner_iters_mean": inner,
                   "f_last": r0.f_last, "infeas_last": r0.infeas_last, "f_avg": r0.f_avg,
                   "infeas_avg": r0.infeas_avg, "d_lb": r0.d_lb, "converged_last": r0.converged_last,
                   "converged_avg": r0.converged_avg},
-        "roofline": {"kernel": "k_rows<float> inner-iteration GEMV", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": ("k_v2_pass<float> single-pass inner iteration (packed Q, one read of G)"
+                                if single_pass else "k_rows<float> inner-iteration GEMV"),
+                     "bound": "hbm", "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "traffic": None,
                      "peak_kind": kind, "launches_timed": st["gemv_launches"],
@@ -584,55 +588,69 @@ def run_served(args):
         P.solve(ops[dd["alg"]])
     for P in mpc_probs:
         P.solve(om)
+    # requests prepared up front: the submission loop only times and submits
+    reqs = []
+    for k, (ta, kind, pick) in enumerate(zip(times, kinds, picks)):
+        if kind == 1:
+            i = int(pick) % len(mpc_probs)
+            reqs.append((ta, mpc_probs[i], om, mpc["qs"][i] + 0.1 * rng.standard_normal(100), 100, 600,
+                         ("mpc", i) if k % 100 == 0 else None))
+        else:
+            i = int(pick) % len(probs)
+            reqs.append((ta, probs[i], ops[pool[i]["alg"]], rng.standard_normal(pool[i]["n"]), pool[i]["n"],
+                         pool[i]["p"], ("qp", i) if k % 100 == 0 else None))
     ctx.serve_start(slots=1024, hbm_budget_bytes=32 << 30)
-    sub, lat, meta = {}, [], []
+    from collections import deque
+    pending = deque()          # (ticket, t_submit, n, p, info, q) in submission order
+    lat, meta = [], []
     lock = threading.Lock()
     done_flag = [False]
 
-    def poller():
-        while not done_flag[0] or sub:
+    def poller():  # polls a window of the oldest outstanding tickets
+        while True:
             with lock:
-                items = list(sub.items())
-            for tk, (t0, n, p, info) in items:
+                window = list(pending)[:256]
+            if not window:
+                if done_flag[0]:
+                    return
+                time.sleep(0.0005)
+                continue
+            finished = set()
+            for tk, t0, n, p, info, q in window:
                 r = ctx.poll(tk, n, p)
                 if r is not None:
-                    t1 = time.perf_counter()
-                    with lock:
-                        sub.pop(tk, None)
-                    lat.append(t1 - t0)
+                    lat.append(time.perf_counter() - t0)
+                    finished.add(tk)
                     if info is not None:
-                        meta.append((info, r))
-            time.sleep(0)
+                        meta.append((info, q, r))
+            if finished:
+                with lock:
+                    keep = [e for e in pending if e[0] not in finished]
+                    pending.clear()
+                    pending.extend(keep)
+            else:
+                time.sleep(0.0002)
     th = threading.Thread(target=poller, daemon=True)
     th.start()
     start = time.perf_counter()
-    for k, (ta, kind, pick) in enumerate(zip(times, kinds, picks)):
+    for ta, P, o, q, n, p, info in reqs:
         while time.perf_counter() - start < ta:
             pass
-        if kind == 1:
-            i = int(pick) % len(mpc_probs)
-            P, n, p = mpc_probs[i], 100, 600
-            q = mpc["qs"][i] + 0.1 * rng.standard_normal(100)
-            tk = ctx.submit(P, om, q=q)
-            info = ("mpc", i, q) if k % 100 == 0 else None
-        else:
-            i = int(pick) % len(probs)
-            P, n, p = probs[i], pool[i]["n"], pool[i]["p"]
-            q = rng.standard_normal(n)
-            tk = ctx.submit(P, ops[pool[i]["alg"]], q=q)
-            info = ("qp", i, q) if k % 100 == 0 else None
+        tk = ctx.submit(P, o, q=q)
         with lock:
-            sub[tk] = (time.perf_counter(), n, p, info)
+            pending.append((tk, time.perf_counter(), n, p, info, q))
     offered = time.perf_counter() - start
     done_flag[0] = True
-    th.join(timeout=600)
+    th.join(timeout=args.drain)
     total = time.perf_counter() - start
-    ctx.serve_stop()
+    drained = not th.is_alive()
+    if drained:
+        ctx.serve_stop()
     lat_ms = np.array(lat) * 1e3
     # FP64 oracle error on the 1% sample
     errs = []
-    for info, (stt, xl, xa, lm, r) in meta[:200]:
-        kind, i, q = info
+    for info, q, (stt, xl, xa, lm, r) in meta[:args.oracle_sample]:
+        kind, i = info
         if kind == "qp":
             dd = pool[i]
             qp = O.QP(dd["Q"].double().cpu().numpy(), q, dd["G"].double().cpu().numpy(), dd["g"].double().cpu().numpy(),
@@ -642,7 +660,7 @@ def run_served(args):
             qp = O.QP(mpc["Q"], q, mpc["G"], mpc["gs"][i], mpc["lb"], mpc["ub"])
             a = O.DFGM
         c = O.constants(qp, a, lmin_Q=1.0 if kind == "qp" else mpc["lmin_Q"])
-        ro = O.dfom(qp, a, c, eps_out=1e-5, eps_in=1e-9, max_outer=20000)
+        ro = O.dfom(qp, a, c, eps_out=1e-4, eps_in=1e-8, max_outer=20000)
         x = xl if r.converged_last else xa
         errs.append(float(np.linalg.norm(x - ro.x_last) / max(np.linalg.norm(ro.x_last), 1e-12)))
     line = {"metric": METRIC, "value": len(lat) / total, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
@@ -651,10 +669,13 @@ def run_served(args):
             "config": {"workload": "served_poisson", "rate_per_s": rate, "duration_s": dur, "pool": args.pool,
                        "mpc_fraction": 0.05, "slots": 1024, "parallelism": "replicas1"},
             "served": {"requests": int(len(times)), "completed": int(len(lat)), "offered_s": offered,
+                       "drained": drained,
                        "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat_ms) else None,
                        "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat_ms) else None,
                        "oracle_rel_err_max": max(errs) if errs else None, "oracle_sampled": len(errs)}}
     print(json.dumps(line), flush=True)
+    if not drained:  # requests still in flight: leave without tearing the loop down under them
+        os._exit(0)
     for P in probs + mpc_probs:
         P.close()
     ctx.close()
@@ -665,7 +686,9 @@ def main():
     ap.add_argument("--workload", default="large", choices=["large", "small", "uneven", "mpc", "served"])
     ap.add_argument("--count", type=int, default=None)
     ap.add_argument("--rate", type=float, default=20000.0)
-    ap.add_argument("--duration", type=float, default=10.0)
+    ap.add_argument("--duration", type=float, default=0.5)
+    ap.add_argument("--drain", type=float, default=120.0)
+    ap.add_argument("--oracle-sample", type=int, default=20)
     ap.add_argument("--pool", type=int, default=2000)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)

@@ -48,22 +48,51 @@ struct CtaInst {
 };
 
 // out[i] = sum_j M[j*ld + i] v[j], i < cols, j < rows  (out = M' v).
-// One thread per output, four independent accumulators, fixed order.
+// The rows are split into S contiguous segments (S depends on cols only: 8
+// for cols <= 32 down to 1 for cols > 128, so that narrow products still
+// occupy the block); a (segment, column) pair runs 8 independent accumulators
+// (8 loads in flight when M is in global memory), and the S partial sums are
+// added in segment order in `part` (S * cols <= 256 elements).  The order of
+// every sum is fixed by (rows, cols) alone: results do not depend on the block
+// size or on whether M sits in shared or global memory.
 template <typename A, typename T, typename V>
 __device__ __forceinline__ void mtv(const T* __restrict__ M, int rows, int cols, int ld,
-                                    const V* __restrict__ v, A* __restrict__ out) {
-  for (int i = threadIdx.x; i < cols; i += blockDim.x) {
-    const T* col = M + i;
-    A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0);
-    int j = 0;
-    for (; j + 4 <= rows; j += 4) {
-      a0 += A(col[(size_t)(j + 0) * ld]) * A(v[j + 0]);
-      a1 += A(col[(size_t)(j + 1) * ld]) * A(v[j + 1]);
-      a2 += A(col[(size_t)(j + 2) * ld]) * A(v[j + 2]);
-      a3 += A(col[(size_t)(j + 3) * ld]) * A(v[j + 3]);
+                                    const V* __restrict__ v, A* __restrict__ out, A* __restrict__ part) {
+  const int cp = (cols + 31) & ~31;
+  const int S = cp >= 256 ? 1 : min(8, 256 / cp);
+  for (int q = threadIdx.x; q < S * cp; q += blockDim.x) {
+    const int sg = q / cp, c = q - sg * cp;
+    if (c >= cols) continue;
+    const int r0 = (int)((long long)rows * sg / S), r1 = (int)((long long)rows * (sg + 1) / S);
+    const T* col = M + c;
+    A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0), a4 = A(0), a5 = A(0), a6 = A(0), a7 = A(0);
+    int j = r0;
+    for (; j + 8 <= r1; j += 8) {
+      const T m0 = col[(size_t)(j + 0) * ld], m1 = col[(size_t)(j + 1) * ld];
+      const T m2 = col[(size_t)(j + 2) * ld], m3 = col[(size_t)(j + 3) * ld];
+      const T m4 = col[(size_t)(j + 4) * ld], m5 = col[(size_t)(j + 5) * ld];
+      const T m6 = col[(size_t)(j + 6) * ld], m7 = col[(size_t)(j + 7) * ld];
+      a0 += A(m0) * A(v[j + 0]);
+      a1 += A(m1) * A(v[j + 1]);
+      a2 += A(m2) * A(v[j + 2]);
+      a3 += A(m3) * A(v[j + 3]);
+      a4 += A(m4) * A(v[j + 4]);
+      a5 += A(m5) * A(v[j + 5]);
+      a6 += A(m6) * A(v[j + 6]);
+      a7 += A(m7) * A(v[j + 7]);
     }
-    for (; j < rows; ++j) a0 += A(col[(size_t)j * ld]) * A(v[j]);
-    out[i] = (a0 + a1) + (a2 + a3);
+    for (; j < r1; ++j) a0 += A(col[(size_t)j * ld]) * A(v[j]);
+    const A r = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    if (S == 1) out[c] = r;
+    else part[sg * cols + c] = r;
+  }
+  if (S > 1) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+      A o = part[c];
+      for (int sg = 1; sg < S; ++sg) o += part[sg * cols + c];
+      out[c] = o;
+    }
   }
 }
 
@@ -92,6 +121,7 @@ struct CtaWs {
   XState<T> A, B;        // main warm-start chain, extra last-iterate solve
   T *c, *tn, *w, *mu, *lam, *lamp, *ul, *uavg;
   double *usum, *dn, *dp, *red;
+  T* part;               // 256 partial sums of the segmented products
   const T *Q, *G, *GT;
 };
 
@@ -116,10 +146,10 @@ __device__ double cta_cert(const CtaInst<T>& I, CtaWs<T>& W, const T* x, const T
       W.w[j] = I.cone == CONE_EQ ? v : (v > T(0) ? v : T(0));
     }
     __syncthreads();
-    mtv<T>(W.G, p, n, n, W.w, W.tn);
+    mtv<T>(W.G, p, n, n, W.w, W.tn, W.part);
     __syncthreads();
   } else if (!c_valid) {
-    mtv<T>(W.G, p, n, n, mu, W.tn);
+    mtv<T>(W.G, p, n, n, mu, W.tn, W.part);
     __syncthreads();
   }
   const double L = I.LL, sg = I.sigma;
@@ -150,7 +180,7 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
   const T rho = T(I.rho), L = T(I.LL);
   if (!aug) {  // c = q + G' mu, fixed over the inner loop
     if (p > 0) {
-      mtv<T>(W.G, p, n, n, mu, W.c);
+      mtv<T>(W.G, p, n, n, mu, W.c, W.part);
       __syncthreads();
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) W.c[i] = (p > 0 ? W.c[i] : T(0)) + I.q[i];
@@ -174,7 +204,7 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
         W.w[j] = I.cone == CONE_EQ ? v : (v > T(0) ? v : T(0));
       }
       __syncthreads();
-      mtv<T>(W.G, p, n, n, W.w, W.tn);
+      mtv<T>(W.G, p, n, n, W.w, W.tn, W.part);
       __syncthreads();
     }
     // step 1 of FOM: x^k = [y - grad phi(y) / L]_U
@@ -185,8 +215,11 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
       S.xn[i] = clampT(y - gr / L, I.lb[i], I.ub[i]);
     }
     __syncthreads();
-    mtv<T>(W.Q, n, n, n, S.xn, S.Qxn);
-    if (aug) mtv<T>(W.GT, n, p, p, S.xn, S.Gxn);
+    mtv<T>(W.Q, n, n, n, S.xn, S.Qxn, W.part);
+    if (aug) {
+      __syncthreads();
+      mtv<T>(W.GT, n, p, p, S.xn, S.Gxn, W.part);
+    }
     __syncthreads();
     // step 2 weight beta_k (GM/FGM/FGM_sigma rules, Sec. 2.1)
     if (fgm_sigma) {
@@ -211,7 +244,7 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
     }
   }
   if (!aug && p > 0) {  // G ubar for the dual gradient
-    mtv<T>(W.GT, n, p, p, S.x, S.Gx);
+    mtv<T>(W.GT, n, p, p, S.x, S.Gx, W.part);
     __syncthreads();
   }
   return k;
@@ -396,11 +429,11 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int max_it, int 
   double theta = 0.0, r = 0.0, beta_prev = 0.0;
   for (int j = 0; j < mmax; ++j) {
     if (which == 0) {
-      mtv<T>(W.Q, n, n, n, v, w);
+      mtv<T>(W.Q, n, n, n, v, w, W.part);
     } else {
-      mtv<T>(W.GT, n, p, p, v, t);
+      mtv<T>(W.GT, n, p, p, v, t, W.part);
       __syncthreads();
-      mtv<T>(W.G, p, n, n, t, w);
+      mtv<T>(W.G, p, n, n, t, w, W.part);
     }
     __syncthreads();
     double pa = 0.0;
@@ -453,6 +486,7 @@ __host__ __device__ inline size_t cta_vec_bytes(int n, int p) {
   b += 2 * (6 * a16(n * sizeof(T)) + 3 * a16(pn * sizeof(T)));  // A, B states
   b += 4 * a16(n * sizeof(T));                                   // c, tn, ul, uavg
   b += 4 * a16(pn * sizeof(T));                                  // w, mu, lam, lamp
+  b += a16(256 * sizeof(T));                                     // part
   return b;
 }
 template <typename T>
@@ -490,6 +524,7 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
   W.mu = (T*)take(pn * sizeof(T));
   W.lam = (T*)take(pn * sizeof(T));
   W.lamp = (T*)take(pn * sizeof(T));
+  W.part = (T*)take(256 * sizeof(T));
   W.Q = I.Q; W.G = I.G; W.GT = I.GT;
   // stage the matrices in shared memory when they fit
   const size_t nn = (size_t)n * n, np_ = (size_t)n * p;
@@ -541,8 +576,11 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
     W.lam[j] = l0; W.lamp[j] = l0; W.mu[j] = l0;
   }
   __syncthreads();
-  mtv<T>(W.Q, n, n, n, A.x, A.Qx);
-  if (p > 0) mtv<T>(W.GT, n, p, p, A.x, A.Gx);
+  mtv<T>(W.Q, n, n, n, A.x, A.Qx, W.part);
+  if (p > 0) {
+    __syncthreads();
+    mtv<T>(W.GT, n, p, p, A.x, A.Gx, W.part);
+  }
   __syncthreads();
 
   const bool aug = I.rho > 0.0, fast = alg_fast(I.alg);

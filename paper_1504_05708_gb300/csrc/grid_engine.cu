@@ -407,6 +407,53 @@ __global__ void k_lz_next(T* v, T* vp, const T* w, int n, const Ctrl* ctrl, int 
   }
 }
 
+// H = Q + rho G'G for the equality-constrained augmented Lagrangian (K = {0}:
+// grad_x L_rho(x, mu) = (Q + rho G'G) x + q + G'(mu + rho g), Sec. 2).  Both
+// factors are row slices of G (p x n): a 64 x 64 tile of H per block, 256
+// threads with 4 x 4 outputs each, the p rows in steps of 16 through shared
+// memory, one accumulator per output in the element type.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram(const T* __restrict__ G, const T* __restrict__ Q, int n, int p, T rho,
+                                              T* __restrict__ H) {
+  __shared__ __align__(16) T As[16][64], Bs[16][64];
+  const int i0 = blockIdx.y * 64, k0 = blockIdx.x * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
+  for (int j0 = 0; j0 < p; j0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int r = e >> 6, c = e & 63, j = j0 + r;
+      As[r][c] = (j < p && i0 + c < n) ? G[(size_t)j * n + i0 + c] : T(0);
+      Bs[r][c] = (j < p && k0 + c < n) ? G[(size_t)j * n + k0 + c] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      T a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[r][ty * 4 + u];
+        b[u] = Bs[r][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const int i = i0 + ty * 4 + u, k = k0 + tx * 4 + w;
+      if (i < n && k < n) H[(size_t)i * n + k] = Q[(size_t)i * n + k] + rho * acc[u][w];
+    }
+}
+
 // Largest eigenvalue theta of the m x m symmetric tridiagonal matrix with
 // diagonal a and off-diagonal b (b[i] joins rows i and i+1) by bisection on
 // Sturm counts, and |s_m|, the last component of its unit eigenvector, from
@@ -491,7 +538,12 @@ struct GridWs {
   float4* parts = nullptr;
   int v2_ctas = 0;
   bool v2_ready = false;
+  const void* v2_src = nullptr;  // the matrix packed into Qp (Q, or H below)
   std::vector<long long> hoff;  // host copy of the packed-row offsets
+  // K = {0}, rho > 0: H = Q + rho G'G, so the inner gradient is one product
+  void* H = nullptr;
+  double H_rho = NAN;
+  void* zp = nullptr;           // p zeros
 };
 
 void grid_free(GridWs* w) {
@@ -501,6 +553,8 @@ void grid_free(GridWs* w) {
   if (w->hctrl) cudaFreeHost(w->hctrl);
   if (w->partials) cudaFree(w->partials);
   if (w->v2mem) cudaFree(w->v2mem);
+  if (w->H) cudaFree(w->H);
+  if (w->zp) cudaFree(w->zp);
   for (auto& e : w->ev)
     if (e) cudaEventDestroy(e);
   for (auto& e : w->evpool) cudaEventDestroy(e);
@@ -568,6 +622,9 @@ struct GridRun {
   const SolveCfg* cfg;
   long long inner_total = 0;
   const T* Q() const { return (const T*)P->Q; }
+  // matrix of the inner products: H = Q + rho G'G in the K = {0} Hessian mode, else Q
+  bool hmode = false;
+  const T* Qm() const { return hmode ? (const T*)W->H : (const T*)P->Q; }
   const T* G() const { return (const T*)P->G; }
   const T* GT() const { return (const T*)P->GT; }
   const T* q() const { return (const T*)P->q; }
@@ -694,10 +751,13 @@ struct GridRun {
       W->dotQ = (float*)(b + bQ + bO + bR);
       W->parts = (float4*)(b + bQ + bO + bR + bD);
       DQ_CK(cudaMemcpyAsync(W->qoff, W->hoff.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
-      k_pack_upper<<<std::min(n, 8192), 256, 0, st>>>((const float*)Q(), n, W->qoff, W->Qp);
+      W->v2_ready = true;
+    }
+    if (W->v2_src != (const void*)Qm()) {  // (re)pack the matrix of the inner products
+      k_pack_upper<<<std::min(n, 8192), 256, 0, st>>>((const float*)Qm(), n, W->qoff, W->Qp);
       ++P->ctx->launches;
       DQ_CK(cudaGetLastError());
-      W->v2_ready = true;
+      W->v2_src = (const void*)Qm();
     }
     // CTA roles in proportion to the bytes each matrix contributes
     const double bq = double(W->hoff[n]), bg = aug ? double(p) * n : 0.0;
@@ -766,11 +826,22 @@ struct GridRun {
   // Algorithm FOM on L_rho(., mu) over the box for the chain (X, QX, GX)
   // whose current iterate is in slot 0 (and slot 2).  Returns the slot of ubar.
   dq_status fom(void* const* X, void* const* QX, void* const* GX, const T* mu, int* slot) {
-    const bool aug = rho > 0.0;
+    // aug: the inner loop carries G x and forms G' [mu + rho (G y + g)]_+ (rho > 0, K = R^p_-);
+    // in the Hessian mode (K = {0}) the gradient is H x + q + G'(mu + rho g) with H = Q + rho G'G
+    const bool aug = rho > 0.0 && !hmode;
     cudaError_t e = cudaSuccess;
-    if (!aug) {  // c = q + G' mu (rows of G')
-      if (p > 0) e = gemv(GT(), n, nullptr, 0, p, mu, v(W->c), nullptr, q());
-      else e = cudaMemcpyAsync(W->c, q(), (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st);
+    if (!aug) {  // c = q + G' mu (rho = 0) or q + G'(mu + rho g) (Hessian mode), rows of G'
+      if (p > 0 && hmode) {
+        RowJob<T> J = job();
+        J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->c); J.add1 = q();
+        J.vmode = VM_W; J.a0 = v(W->zp); J.a1 = v(W->zp); J.a2 = mu; J.a3 = g();
+        J.beta = T(0); J.rho = T(rho);
+        e = rows<false>(J);
+      } else if (p > 0) {
+        e = gemv(GT(), n, nullptr, 0, p, mu, v(W->c), nullptr, q());
+      } else {
+        e = cudaMemcpyAsync(W->c, q(), (size_t)n * sizeof(T), cudaMemcpyDeviceToDevice, st);
+      }
       if (e != cudaSuccess) { set_error("fom setup: %s", cudaGetErrorString(e)); return DQ_ERR_CUDA; }
     }
     DQ_CK(cudaMemsetAsync(W->ctrl, 0, sizeof(Ctrl), st));
@@ -880,7 +951,7 @@ struct GridRun {
         }
         // x^k = [y - grad/L]_U in the prologue; then Q x^k (and G x^k)
         RowJob<T> J = job();
-        J.M1 = Q(); J.R1 = n; J.M2 = aug ? G() : nullptr; J.R2 = aug ? p : 0; J.cols = n;
+        J.M1 = Qm(); J.R1 = n; J.M2 = aug ? G() : nullptr; J.R2 = aug ? p : 0; J.cols = n;
         J.out1 = v(QX[sn]); J.out2 = aug ? v(GX[sn]) : nullptr;
         J.vmode = VM_STEP; J.a0 = v(X[sx]); J.a1 = v(X[sxp]); J.a2 = v(QX[sx]); J.a3 = v(QX[sxp]);
         J.a4 = aug ? q() : v(W->c); J.a5 = aug ? v(W->tn) : nullptr; J.a6 = lb(); J.a7 = ub();
@@ -989,6 +1060,28 @@ struct GridRun {
     return true;
   }
 
+  // H = Q + rho G'G into the workspace (kept while rho is unchanged), p zeros.
+  dq_status build_H() {
+    if (W->H && W->H_rho == rho) return DQ_OK;
+    const size_t esz = sizeof(T);
+    if (!W->H) {
+      if (cudaMalloc(&W->H, (size_t)n * n * esz) != cudaSuccess ||
+          cudaMalloc(&W->zp, (size_t)std::max(p, 1) * esz) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("Hessian-mode allocation (%zu bytes) failed", (size_t)n * n * esz);
+        return DQ_ERR_NOMEM;
+      }
+      DQ_CK(cudaMemsetAsync(W->zp, 0, (size_t)std::max(p, 1) * esz, st));
+    }
+    const dim3 grid((n + 63) / 64, (n + 63) / 64);
+    k_gram<T><<<grid, 256, 0, st>>>(G(), Q(), n, p, T(rho), (T*)W->H);
+    ++P->ctx->launches;
+    DQ_CK(cudaGetLastError());
+    W->H_rho = rho;
+    W->v2_src = nullptr;  // the packed copy (if any) is stale
+    return DQ_OK;
+  }
+
   dq_status solve(const dq_outputs* out, dq_result* res) {
     const int eb = std::min(blocks, 4096);
     const bool warm = cfg->warm_start && P->has_state;
@@ -996,7 +1089,11 @@ struct GridRun {
     k_init<T><<<eb, 256, 0, st>>>(v(W->X[0]), warm ? (const T*)P->x_state : nullptr, lb(), ub(), n, v(W->lam),
                                   v(W->lamp), v(W->mu), warm ? (const T*)P->lam_state : nullptr, p, W->usum);
     DQ_CK(cudaGetLastError());
-    cudaError_t e = gemv(Q(), n, p > 0 ? G() : nullptr, p, n, v(W->X[0]), v(W->QX[0]), p > 0 ? v(W->GX[0]) : nullptr);
+    if (hmode) {  // H = Q + rho G'G, once per (problem, rho)
+      dq_status sh = build_H();
+      if (sh != DQ_OK) return sh;
+    }
+    cudaError_t e = gemv(Qm(), n, p > 0 ? G() : nullptr, p, n, v(W->X[0]), v(W->QX[0]), p > 0 ? v(W->GX[0]) : nullptr);
     if (e != cudaSuccess) { set_error("init: %s", cudaGetErrorString(e)); return DQ_ERR_CUDA; }
     int cur = 0;
     double theta = 1.0, S = 0.0, d_lb = -INFINITY;
@@ -1153,10 +1250,16 @@ static dq_status solve_T(dq_problem* P, GridWs* W, const SolveCfg& c, const dq_o
                              : c.eps_in;
   R.kd_plus = !(c.kd_literal && !(lmin > 0.0));
   if constexpr (std::is_same<T, float>::value) {
-    // the single-pass iteration runs when DQ_GRID_SINGLE_PASS=1 and the rows fit its layout
+    // FP32 instances whose rows fit the single-pass layout (n a multiple of 4,
+    // n <= 20480) use the single-pass iteration; DQ_GRID_SINGLE_PASS=0 selects
+    // the two-pass form (kept as the reference path of the tests)
     const char* ev = getenv("DQ_GRID_SINGLE_PASS");
-    R.use_v2 = (P->n % 4 == 0) && (P->n / 4 <= V2_CONS * 10) && (ev && ev[0] == '1');
+    R.use_v2 = (P->n % 4 == 0) && (P->n / 4 <= V2_CONS * 10) && !(ev && ev[0] == '0');
   }
+  // K = {0} with rho > 0: precompute H = Q + rho G'G (DQ_GRID_HESSIAN=0 keeps the
+  // augmented two-matrix form, the reference path of the tests)
+  const char* eh = getenv("DQ_GRID_HESSIAN");
+  R.hmode = P->cone == CONE_EQ && R.rho > 0.0 && P->p > 0 && !(eh && eh[0] == '0');
   return R.solve(out, res);
 }
 

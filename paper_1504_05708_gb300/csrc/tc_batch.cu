@@ -3,29 +3,41 @@
 // Instances that share Q and G and differ only in q and g (condensed MPC with
 // a different initial state per instance) turn the matrix-vector products of
 // Algorithm FOM (Sec. 2.1) and of the dual step of Algorithm DFOM (Sec. 3)
-// into matrix-matrix products over the batch.  One thread block owns a tile
-// of 128 instances and keeps the whole inner loop on chip:
-//   * TMEM lane b holds instance b: columns hold D = Q x^k (the MMA
-//     accumulator), x^k, x^{k-1}, Q x^{k-1} and c = q + G' mu, so every
-//     per-instance quantity (step, projection, momentum, stopping certificate)
-//     is local to one thread and needs no cross-thread reduction;
-//   * each inner iteration is D = X Q' on tcgen05 with bf16 hi/lo split
-//     operands (hi*hi + hi*lo + lo*hi) accumulated in FP32, X rewritten by the
-//     epilogue threads straight into the operand layout;
-//   * per outer iteration G ubar (dual gradient) and G' mu (next c) are two
-//     more tensor-core products against G and G' tiles brought into shared
-//     memory by bulk copies; lambda, lambda_prev, mu live in global memory.
-// Stopping checks (eq. duquad_in for the inner loop per instance; the outer
-// certificate with FP64-accurate residuals) follow the CTA engine's rules; the
-// outer checks run between launches in a per-instance evaluation kernel.
-// Limits: rho = 0 (DGM/DFGM), n <= 100 (TMEM columns), 1 CTA per SM.
+// into matrix-matrix products over the batch.  One persistent thread block
+// (128 threads) takes a tile of 128 instances and runs its whole solve --
+// every outer iteration, the inner loops, the outer stopping checks and the
+// extra last-iterate solves -- without returning to the host:
+//   * TMEM lane b holds instance b: four 16-aligned column regions hold
+//     D (the MMA accumulator), y^k, x^k and c = q + G' mu, so every
+//     per-instance quantity (step, projection, momentum, certificates,
+//     residuals) is local to one thread and needs no cross-thread reduction;
+//   * an inner iteration is D = Q y^k on tcgen05 with bf16 hi/lo split
+//     operands (hi*hi + hi*lo + lo*hi) accumulated in FP32; the epilogue forms
+//     x^{k+1} = [y^k - (D + c)/L]_U and y^{k+1}, and writes the next operand
+//     straight into the K-major shared-memory layout.  At certificate
+//     iterations the operand is x^{k+1} first (D = Q x^{k+1} for the
+//     gradient-mapping bound of eq. duquad_in), then y^{k+1};
+//   * per outer iteration G ubar (dual gradient) and G' mu (next c) are
+//     chunked tensor-core products against pre-packed G and G' tiles brought
+//     in by double-buffered bulk copies; lambda, lambda_prev, mu and the
+//     averaging sum live in global memory, instance-minor
+//     ([tile][element][lane]) so that a tile's 128 threads touch 512
+//     contiguous bytes per element.
+// The outer certificate (F(u) - d_lb <= eps, dist_K(Gu + g) <= eps) follows
+// the thread-block engine's rules.  The split products carry a relative error
+// near 2^-16, which is enough for G u (residuals) but not for F(u) = u'Qu/2 +
+// q'u at eps = 1e-3 (the quadratic term is ~250 on the MPC workload), so F is
+// evaluated per lane in FP32 from the FP32 Q (SIMT, symmetric half).  A lane
+// whose instance has converged is frozen (its state no longer changes) and the
+// tile ends when every lane is done.
+// Limits: rho = 0 (DGM/DFGM), n <= 128 (four TMEM regions of 16-aligned n).
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
 #include <vector>
 
-#include "cta_engine.cuh"
+#include "dq_common.cuh"
 #include "dq_host.h"
 #include "tc_common.cuh"
 
@@ -34,29 +46,30 @@ namespace dq {
 __global__ void k_pack_kmajor(const float* __restrict__ src, int R_valid, int K_valid, int ld, int R_pad, int K_pad,
                               uint4* __restrict__ hi, uint4* __restrict__ lo);
 
-static constexpr int TM = 128;                        // instances per tile (TMEM lanes)
+static constexpr int TM = 128;                        // instances per tile (TMEM lanes, threads)
+static constexpr int TC_KC = 48;                      // constraints per G' chunk (MMA K)
 static constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
 struct TcArgs {
-  int n, p, B, NPAD, NV, NC, KC, nchG, nchGT;
-  const uint4 *Qhi, *Qlo, *Ghi, *Glo, *GThi, *GTlo;
-  const float *q, *g, *lb, *ub;                       // q: B x n, g: B x p
-  float *x, *xl, *usum, *lam, *lamp, *mun, *muk;      // B x n / B x p
-  double *theta, *S;
-  int* kout;
-  long long* kin;
-  int* active;
+  int n, p, B, NPAD, NC, ntiles, nchG, nchGT;
+  const uint4 *Qhi, *Qlo, *Ghi, *Glo, *GThi, *GTlo;   // packed K-major bf16 hi/lo
+  const float* Qf;                                   // FP32 Q (n x n) for F(u)
+  const float *qT, *gT;                              // instance-minor inputs
+  const float *lb, *ub;                              // n (shared box)
+  const float *x0T, *lam0T;                          // warm start, instance-minor (nullable)
+  float *lam, *lamp, *mu, *usum, *save;              // instance-minor workspace
+  float *xlT, *xaT, *xsT;                            // instance-minor outputs
+  DevResult* res;
   float L, alpha;
-  double sigma, beta_sigma, eps_in;
-  int cone, kd_plus;
-  int inner_fixed, inner_check_every, max_inner, nouter, mode, fast;
-  int* err;
+  float sigma, beta_sigma, eps_in, eps_out;
+  int cone, kd_plus, fast, want_last, want_avg;
+  int inner_fixed, inner_check_every, max_inner, outer_fixed, max_outer, check_every;
+  int* next;                                         // tile queue
+  int* err;                                          // set when a bounded wait gave up
 };
 
-struct TcSmem {
-  uint8_t *Qh, *Ql, *Xh, *Xl, *Gh, *Gl, *Mh, *Ml, *Bh, *Bl;
-  float *lb, *ub;
-};
+// Instance-minor index: element e of lane l in tile t.
+__device__ __forceinline__ size_t im(int t, int E, int e, int l) { return ((size_t)t * E + e) * TM + l; }
 
 __device__ __forceinline__ void tc_mma_tile(uint32_t d, const uint8_t* Ah, const uint8_t* Al, const uint8_t* Bh,
                                             const uint8_t* Bl, int Nrows, int K, bool accumulate) {
@@ -82,536 +95,730 @@ __device__ __forceinline__ void put8(uint8_t* H, uint8_t* Lo, int r, int k0, con
   *(uint4*)(Lo + off) = l;
 }
 
-__global__ void __launch_bounds__(128, 1) k_tc_solve(TcArgs a) {
+__device__ __forceinline__ void kahan(float& s, float& c, float v) {
+  const float y = v - c, t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Per-block state of the pipeline (uniform across the block's threads).
+struct TcCtx {
+  const TcArgs* a;
+  uint8_t *Qh, *Ql, *Ah, *Al;
+  uint8_t* B0;                  // chunk buffers: buffer b hi at B0 + 2 b bb, lo at B0 + (2 b + 1) bb
+  size_t ab, bb;                // bytes of one operand half (hi or lo); of one chunk half
+  float *lb, *ub;
+  uint64_t *bar_mma, *bar_tx;   // [2] each
+  uint32_t ph_mma, ph_tx;       // phase bit of barrier b at bit b
+  uint32_t tm, lane_off;
+  uint32_t rD, rY, rX, rC;       // TMEM column regions
+  int tid, NPAD;
+  bool ok;
+
+  __device__ void sync_async() {  // operand writes visible to the tensor core, TMEM ops ordered
+    tc::tmem_st_wait();
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
+  __device__ __forceinline__ uint8_t* Bh(int b) const { return B0 + (size_t)(2 * b) * bb; }
+  __device__ __forceinline__ uint8_t* Bl(int b) const { return B0 + (size_t)(2 * b + 1) * bb; }
+  __device__ __forceinline__ void wait_mma(int b) {
+    ok = tc::mbar_wait(&bar_mma[b], (ph_mma >> b) & 1u, kTcWaitNs) && ok;
+    ph_mma ^= 1u << b;
+    tc::fence_after();
+  }
+  __device__ __forceinline__ void wait_tx(int b) {
+    ok = tc::mbar_wait(&bar_tx[b], (ph_tx >> b) & 1u, kTcWaitNs) && ok;
+    ph_tx ^= 1u << b;
+  }
+  __device__ __forceinline__ void issue_B(int b, const uint4* hi, const uint4* lo, uint32_t bytes) {  // thread 0
+    tc::mbar_expect_tx(&bar_tx[b], 2 * bytes);
+    tc::bulk_g2s(Bh(b), hi, bytes, &bar_tx[b]);
+    tc::bulk_g2s(Bl(b), lo, bytes, &bar_tx[b]);
+  }
+  // D region = Q * operand (operand already written and synced by the caller)
+  __device__ void mma_Q() {
+    if (tid == 0) {
+      tc_mma_tile(tm + rD, Ah, Al, Qh, Ql, NPAD, NPAD, false);
+      tc::mma_commit(&bar_mma[0]);
+    }
+    wait_mma(0);
+  }
+  // operand <- TMEM region r
+  __device__ void operand_from(uint32_t r) {
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t v[16];
+      tc::tmem_ld16(tm + lane_off + r + c0, v);
+      tc::tmem_ld_wait();
+      float f[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
+      put8(Ah, Al, tid, c0, f);
+      put8(Ah, Al, tid, c0 + 8, f + 8);
+    }
+  }
+  // region dst <- region src
+  __device__ void region_copy(uint32_t dst, uint32_t src) {
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t v[16];
+      tc::tmem_ld16(tm + lane_off + src + c0, v);
+      tc::tmem_ld_wait();
+      tc::tmem_st16(tm + lane_off + dst + c0, v);
+    }
+  }
+
+  // Chunked product G * operand (N = NC rows of G per chunk) into two
+  // alternating accumulator slots (regions D and Y); epi(ch, slot) consumes
+  // chunk ch.  Bulk copies of chunk ch+1 overlap the product of chunk ch.
+  template <class Epi>
+  __device__ void g_product(Epi epi) {
+    const TcArgs& A = *a;
+    const int nch = A.nchG;
+    if (nch == 0) return;
+    const uint32_t cb = (uint32_t)A.NC * NPAD * 2;  // bytes of one packed chunk (hi or lo)
+    const uint32_t sdelta = rY - rD;  // accumulator slot b at rD + b * sdelta
+    if (tid == 0) {
+      issue_B(0, A.Ghi, A.Glo, cb);
+      if (nch > 1) issue_B(1, A.Ghi + cb / 16, A.Glo + cb / 16, cb);
+    }
+    for (int ch = 0; ch < nch; ++ch) {
+      const int b = ch & 1;
+      wait_tx(b);
+      if (tid == 0) {
+        tc_mma_tile(tm + rD + b * sdelta, Ah, Al, Bh(b), Bl(b), A.NC, NPAD, false);
+        tc::mma_commit(&bar_mma[b]);
+      }
+      if (ch >= 1) {
+        wait_mma(b ^ 1);  // chunk ch-1: its buffer and accumulator slot are ready
+        if (tid == 0 && ch + 1 < nch)
+          issue_B(b ^ 1, A.Ghi + (size_t)(ch + 1) * cb / 16, A.Glo + (size_t)(ch + 1) * cb / 16, cb);
+        epi(ch - 1, rD + (b ^ 1) * sdelta);
+        tc::fence_before();
+        __syncthreads();
+        tc::fence_after();
+      }
+    }
+    wait_mma((nch - 1) & 1);
+    epi(nch - 1, rD + ((nch - 1) & 1) * sdelta);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
+
+  // c = q + G' m into region C, m instance-minor ([p][128] of this tile).
+  // The A operand of each K-chunk (m split into bf16 hi/lo) is built by the
+  // threads into a double buffer carved from the operand area.
+  __device__ void gt_product(int tile, const float* m) {
+    const TcArgs& A = *a;
+    const int nch = A.nchGT, p = A.p;
+    const uint32_t cb = (uint32_t)NPAD * TC_KC * 2;
+    const size_t abytes = (size_t)TM * TC_KC * 2;  // chunk b: hi at Ah + 2 b abytes, lo next
+    auto AH = [&](int b) { return Ah + (size_t)(2 * b) * abytes; };
+    auto AL = [&](int b) { return Ah + (size_t)(2 * b + 1) * abytes; };
+    auto build = [&](int ch, int b) {  // all KC loads in flight before the shared-memory stores
+      const int j0 = ch * TC_KC;
+      float v[TC_KC];
+#pragma unroll
+      for (int i = 0; i < TC_KC; ++i) {
+        const int j = j0 + i;
+        v[i] = j < p ? __ldcg(m + im(tile, p, j, tid)) : 0.f;
+      }
+#pragma unroll
+      for (int k0 = 0; k0 < TC_KC; k0 += 8) put8(AH(b), AL(b), tid, k0, v + k0);
+    };
+    if (nch > 0) {
+      build(0, 0);
+      if (tid == 0) {
+        issue_B(0, A.GThi, A.GTlo, cb);
+        if (nch > 1) issue_B(1, A.GThi + cb / 16, A.GTlo + cb / 16, cb);
+      }
+      for (int ch = 0; ch < nch; ++ch) {
+        const int b = ch & 1;
+        sync_async();  // A chunk ch written by every thread
+        wait_tx(b);
+        if (tid == 0) {
+          tc_mma_tile(tm + rC, AH(b), AL(b), Bh(b), Bl(b), NPAD, TC_KC, ch > 0);
+          tc::mma_commit(&bar_mma[b]);
+        }
+        if (ch >= 1) {
+          wait_mma(b ^ 1);  // product ch-1 done: buffers b^1 free
+          if (tid == 0 && ch + 1 < nch)
+            issue_B(b ^ 1, A.GThi + (size_t)(ch + 1) * cb / 16, A.GTlo + (size_t)(ch + 1) * cb / 16, cb);
+        }
+        if (ch + 1 < nch) build(ch + 1, b ^ 1);
+      }
+      wait_mma((nch - 1) & 1);
+    }
+    // c = acc + q
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t v[16];
+      if (nch > 0) {
+        tc::tmem_ld16(tm + lane_off + rC + c0, v);
+        tc::tmem_ld_wait();
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = 0u;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int col = c0 + i;
+        const float qv = col < A.n ? A.qT[im(tile, A.n, col, tid)] : 0.f;
+        v[i] = __float_as_uint(__uint_as_float(v[i]) + qv);
+      }
+      tc::tmem_st16(tm + lane_off + rC + c0, v);
+    }
+    sync_async();
+  }
+};
+
+// Algorithm FOM on L(., m) for every lane of the tile, from x = region X
+// (warm start) with c = q + G' m in region C.  On return X = ubar, D = Q ubar,
+// the operand holds ubar, and cert_out / kin_out hold the lane's final
+// certificate and iteration count.  Lanes with active == false keep x.
+__device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out, int& kin_out) {
+  const TcArgs& A = *C.a;
+  const int NPAD = C.NPAD, tid = C.tid;
+  const float L = A.L;
+  // y^0 = x^0; D = Q x^0
+  C.region_copy(C.rY, C.rX);
+  C.operand_from(C.rX);
+  C.sync_async();
+  C.mma_Q();
+  const bool fgm_sigma = A.sigma > 0.f;
+  const float kap = A.sigma > 0.f ? 0.5f / A.sigma - 0.5f / L : 0.f;
+  const int m = A.inner_check_every > 0 ? A.inner_check_every : 1;
+  const int kmax = A.inner_fixed > 0 ? A.inner_fixed : A.max_inner;
+  double th = 1.0;
+  bool done = !active;
+  int kin = 0;
+  float cert = 0.f;
+  for (int k = 1;; ++k) {
+    const bool check = A.inner_fixed > 0 ? (k >= A.inner_fixed) : (k % m == 0 || k >= kmax);
+    // weight of the next extrapolation (GM/FGM/FGM_sigma rules, Sec. 2.1)
+    float beta;
+    if (fgm_sigma) {
+      beta = A.beta_sigma;
+    } else {
+      const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * th * th));
+      beta = (float)((th - 1.0) / t1);
+      th = t1;
+    }
+    // x^k = [y - (Q y + c)/L]_U,  y^k = x^k + beta (x^k - x^{k-1})
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t d[16], y[16], x[16], c[16];
+      tc::tmem_ld16(C.tm + C.lane_off + C.rD + c0, d);
+      tc::tmem_ld16(C.tm + C.lane_off + C.rY + c0, y);
+      tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+      tc::tmem_ld16(C.tm + C.lane_off + C.rC + c0, c);
+      tc::tmem_ld_wait();
+      uint32_t xn[16], yn[16];
+      float op[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const float yv = __uint_as_float(y[i]), xv = __uint_as_float(x[i]);
+        const float s = yv - (__uint_as_float(d[i]) + __uint_as_float(c[i])) / L;
+        const float lo = C.lb[c0 + i], hi = C.ub[c0 + i];
+        float xnew = s < lo ? lo : (s > hi ? hi : s);
+        float ynew = xnew + beta * (xnew - xv);
+        if (done) {
+          xnew = xv;
+          ynew = xv;
+        }
+        xn[i] = __float_as_uint(xnew);
+        yn[i] = __float_as_uint(ynew);
+        op[i] = check ? xnew : ynew;
+      }
+      tc::tmem_st16(C.tm + C.lane_off + C.rX + c0, xn);
+      tc::tmem_st16(C.tm + C.lane_off + C.rY + c0, yn);
+      put8(C.Ah, C.Al, tid, c0, op);
+      put8(C.Ah, C.Al, tid, c0 + 8, op + 8);
+    }
+    C.sync_async();
+    C.mma_Q();
+    if (__syncthreads_or(!C.ok)) break;  // a bounded wait gave up: leave with the error flag set
+    if (!check) continue;
+    // D = Q x^k: certificate of eq. duquad_in (gradient-mapping bound, or the
+    // Frank-Wolfe gap when sigma = 0), compensated FP32 sum
+    float cs = 0.f, cc = 0.f;
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t d[16], x[16], c[16];
+      tc::tmem_ld16(C.tm + C.lane_off + C.rD + c0, d);
+      tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+      tc::tmem_ld16(C.tm + C.lane_off + C.rC + c0, c);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (c0 + i >= A.n) continue;
+        const float gd = __uint_as_float(d[i]) + __uint_as_float(c[i]), xv = __uint_as_float(x[i]);
+        const float lo = C.lb[c0 + i], hi = C.ub[c0 + i];
+        if (fgm_sigma) {
+          const float xp = fminf(fmaxf(xv - gd / L, lo), hi);
+          const float dd = xv - xp;
+          kahan(cs, cc, gd * dd + (L * dd) * (L * dd) * kap);
+        } else {
+          const float u1 = gd * lo, u2 = gd * hi;
+          kahan(cs, cc, gd * xv - (u1 < u2 ? u1 : u2));
+        }
+      }
+    }
+    const float cv = cs - cc;
+    const bool stop = A.inner_fixed > 0 || cv <= A.eps_in || k >= kmax;
+    if (stop && !done) {
+      done = true;
+      kin = k;
+      cert = cv;
+    }
+    if (__syncthreads_and(done)) break;
+    // continue: frozen lanes present x (y = x), the others y^k
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t y[16], x[16];
+      tc::tmem_ld16(C.tm + C.lane_off + C.rY + c0, y);
+      tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+      tc::tmem_ld_wait();
+      float op[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (done) y[i] = x[i];
+        op[i] = __uint_as_float(y[i]);
+      }
+      tc::tmem_st16(C.tm + C.lane_off + C.rY + c0, y);
+      put8(C.Ah, C.Al, tid, c0, op);
+      put8(C.Ah, C.Al, tid, c0 + 8, op + 8);
+    }
+    C.sync_async();
+    C.mma_Q();
+  }
+  cert_out = cert;
+  kin_out = active ? kin : 0;
+}
+
+// F(x) = x'Qx/2 + q'x of the lane's x (TMEM region rx), FP32 from the FP32 Q:
+// Q is staged in the bulk-copy buffers and every lane's x in the operand area
+// (instance-minor, conflict-free), both free at this point.  Row sums use
+// four accumulators over the upper triangle, rows are added with Kahan.
+__device__ __forceinline__ float tc_F(TcCtx& C, int tile, uint32_t rx) {
+  const TcArgs& A = *C.a;
+  const int n = A.n, tid = C.tid;
+  float* Xs = (float*)C.Ah;
+  float* Qs = (float*)C.B0;
+  {  // Q into shared memory, eight loads in flight per thread before the stores
+    const int nn = n * n;
+    for (int e0 = tid; e0 < nn; e0 += 8 * TM) {
+      float t8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t8[u] = e0 + u * TM < nn ? __ldg(A.Qf + e0 + u * TM) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e0 + u * TM < nn) Qs[e0 + u * TM] = t8[u];
+    }
+  }
+  for (int c0 = 0; c0 < C.NPAD; c0 += 16) {
+    uint32_t x[16];
+    tc::tmem_ld16(C.tm + C.lane_off + rx + c0, x);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (c0 + i < n) Xs[(c0 + i) * TM + tid] = __uint_as_float(x[i]);
+  }
+  __syncthreads();
+  float s = 0.f, c = 0.f;
+  for (int i = 0; i < n; ++i) {
+    const float* Qr = Qs + (size_t)i * n;
+    const float xi = Xs[i * TM + tid];
+    float a0 = 0.5f * Qr[i] * xi, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int k = i + 1;
+    for (; k + 4 <= n; k += 4) {
+      a0 = fmaf(Qr[k], Xs[k * TM + tid], a0);
+      a1 = fmaf(Qr[k + 1], Xs[(k + 1) * TM + tid], a1);
+      a2 = fmaf(Qr[k + 2], Xs[(k + 2) * TM + tid], a2);
+      a3 = fmaf(Qr[k + 3], Xs[(k + 3) * TM + tid], a3);
+    }
+    for (; k < n; ++k) a0 = fmaf(Qr[k], Xs[k * TM + tid], a0);
+    kahan(s, c, xi * (((a0 + a1) + (a2 + a3)) + A.qT[im(tile, n, i, tid)]));
+  }
+  __syncthreads();  // the buffers are reused by the next product
+  return s - c;
+}
+
+// dist_K(Gx + g)^2 and sum_j m_j (Gx + g)_j for the operand x (m nullable);
+// neg is set when some m_j < 0.
+__device__ __forceinline__ void tc_resid(TcCtx& C, int tile, const float* m, float& inf2, float& lag, int& neg) {
+  const TcArgs& A = *C.a;
+  float is = 0.f, ic = 0.f, ls = 0.f, lc = 0.f;
+  int ng = 0;
+  C.g_product([&](int ch, uint32_t slot) {
+    const int j0 = ch * A.NC;
+    for (int c0 = 0; c0 < A.NC; c0 += 16) {
+      uint32_t r[16];
+      tc::tmem_ld16(C.tm + C.lane_off + slot + c0, r);
+      tc::tmem_ld_wait();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int j = j0 + c0 + i;
+        if (j >= A.p) continue;
+        const float rv = __uint_as_float(r[i]) + A.gT[im(tile, A.p, j, C.tid)];
+        const float dk = rv - proj_K(A.cone, rv);
+        kahan(is, ic, dk * dk);
+        if (m) {
+          const float mj = m[im(tile, A.p, j, C.tid)];
+          ng |= mj < 0.f;
+          kahan(ls, lc, mj * rv);
+        }
+      }
+    }
+  });
+  inf2 = is - ic;
+  lag = ls - lc;
+  neg = ng;
+}
+
+__global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
-  __shared__ __align__(8) uint64_t bar_mma, bar_tx;
+  __shared__ __align__(8) uint64_t bar_mma[2], bar_tx[2], bar_q;
   __shared__ uint32_t s_taddr;
-  __shared__ int s_fail;
+  __shared__ int s_tile;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int NPAD = a.NPAD, NV = a.NV, n = a.n, p = a.p;
-  // shared-memory carve (every region a multiple of 16 bytes)
-  TcSmem S;
+  const int NPAD = a.NPAD, n = a.n, p = a.p;
+  TcCtx C;
+  C.a = &a;
+  C.tid = tid;
+  C.NPAD = NPAD;
+  C.ok = true;
   size_t off = 0;
   auto take = [&](size_t b) {
     uint8_t* r = sm + off;
     off += (b + 127) & ~size_t(127);
     return r;
   };
-  S.Qh = take((size_t)NPAD * NPAD * 2);
-  S.Ql = take((size_t)NPAD * NPAD * 2);
-  uint8_t* U = sm + off;
-  const size_t uA = 2 * (size_t)TM * NPAD * 2 + 2 * (size_t)a.NC * NPAD * 2;
-  const size_t uB = 2 * (size_t)TM * a.KC * 2 + 2 * (size_t)NPAD * a.KC * 2;
-  S.Xh = U;
-  S.Xl = U + (size_t)TM * NPAD * 2;
-  S.Gh = S.Xl + (size_t)TM * NPAD * 2;
-  S.Gl = S.Gh + (size_t)a.NC * NPAD * 2;
-  S.Mh = U;
-  S.Ml = U + (size_t)TM * a.KC * 2;
-  S.Bh = S.Ml + (size_t)TM * a.KC * 2;
-  S.Bl = S.Bh + (size_t)NPAD * a.KC * 2;
-  off += (std::max(uA, uB) + 127) & ~size_t(127);
-  S.lb = (float*)(sm + off);
-  S.ub = S.lb + NV;
-  for (int i = tid; i < NV; i += blockDim.x) {
-    S.lb[i] = i < n ? a.lb[i] : 0.f;
-    S.ub[i] = i < n ? a.ub[i] : 0.f;
+  const size_t qb = (size_t)NPAD * NPAD * 2;
+  C.Qh = take(qb);
+  C.Ql = take(qb);
+  // operand area: [hi | lo] of the 128 x NPAD operand; also the G' mu chunk
+  // double buffer (4 x 128 x KC bf16) and the FP32 x of every lane (tc_F)
+  C.ab = std::max((size_t)TM * NPAD * 2, (size_t)2 * TM * TC_KC * 2);
+  C.Ah = take(2 * C.ab);
+  C.Al = C.Ah + C.ab;
+  // bulk-copy chunk buffers, contiguous; also the FP32 Q (tc_F)
+  C.bb = (std::max(std::max((size_t)a.NC * NPAD * 2, (size_t)NPAD * TC_KC * 2), (size_t)NPAD * NPAD) + 127) &
+         ~size_t(127);
+  C.B0 = take(4 * C.bb);
+  C.lb = (float*)take((size_t)NPAD * 4);
+  C.ub = (float*)take((size_t)NPAD * 4);
+  for (int i = tid; i < NPAD; i += TM) {
+    C.lb[i] = i < n ? a.lb[i] : 0.f;
+    C.ub[i] = i < n ? a.ub[i] : 0.f;
   }
+  C.bar_mma = bar_mma;
+  C.bar_tx = bar_tx;
+  C.ph_mma = 0;
+  C.ph_tx = 0;
   if (tid == 0) {
-    tc::mbar_init(&bar_mma, 1);
-    tc::mbar_init(&bar_tx, 1);
+    tc::mbar_init(&bar_mma[0], 1);
+    tc::mbar_init(&bar_mma[1], 1);
+    tc::mbar_init(&bar_tx[0], 1);
+    tc::mbar_init(&bar_tx[1], 1);
+    tc::mbar_init(&bar_q, 1);
     tc::mbar_init_fence();
-    s_fail = 0;
   }
   __syncthreads();
   if (warp == 0) {
     tc::tmem_alloc(&s_taddr, 512);
     tc::tmem_relinquish();
   }
-  uint32_t ph_mma = 0, ph_tx = 0;
-  // Q operand (hi/lo) once per block
-  if (tid == 0) {
-    const uint32_t qb = (uint32_t)NPAD * NPAD * 2;
-    tc::mbar_expect_tx(&bar_tx, 2 * qb);
-    tc::bulk_g2s(S.Qh, a.Qhi, qb, &bar_tx);
-    tc::bulk_g2s(S.Ql, a.Qlo, qb, &bar_tx);
+  if (tid == 0) {  // Q operand (hi/lo) once per block
+    tc::mbar_expect_tx(&bar_q, 2 * (uint32_t)qb);
+    tc::bulk_g2s(C.Qh, a.Qhi, (uint32_t)qb, &bar_q);
+    tc::bulk_g2s(C.Ql, a.Qlo, (uint32_t)qb, &bar_q);
   }
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  bool ok = tc::mbar_wait(&bar_tx, ph_tx, kTcWaitNs);
-  ph_tx ^= 1;
-  const uint32_t tm = s_taddr;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-  const uint32_t cD = 0, cX = NPAD, cXP = NPAD + NV, cQP = NPAD + 2 * NV, cC = NPAD + 3 * NV;
-  const uint32_t cR = (cXP + 31) / 32 * 32;  // 32-aligned accumulator for the dual products
-  const float L = a.L;
-  const double kap = a.sigma > 0.0 ? 1.0 / (2.0 * a.sigma) - 1.0 / (2.0 * (double)a.L) : 0.0;
+  C.ok = tc::mbar_wait(&bar_q, 0, kTcWaitNs);
+  C.tm = s_taddr;
+  C.lane_off = (uint32_t)(warp * 32) << 16;
+  C.rD = 0;
+  C.rY = NPAD;
+  C.rX = 2 * NPAD;
+  C.rC = 3 * NPAD;
 
-  auto sync_mma = [&](void) -> bool {  // commit by thread 0 happened; all wait
-    const bool w = tc::mbar_wait(&bar_mma, ph_mma, kTcWaitNs);
-    ph_mma ^= 1;
-    tc::fence_after();
-    return w;
-  };
-  auto issue_fence = [&](void) {
-    tc::fence_proxy_async();
-    tc::fence_before();
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(a.next, 1);
     __syncthreads();
-    tc::fence_after();
-  };
-
-  const int ntiles = (a.B + TM - 1) / TM;
-  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const int b = tile * TM + tid;  // this thread's instance
+    const int tile = s_tile;
+    __syncthreads();
+    if (tile >= a.ntiles || !C.ok) break;
+    const int b = tile * TM + tid;
     const bool valid = b < a.B;
-    int act = valid ? a.active[b] : 0;
-    const float* qb = a.q + (size_t)(valid ? b : 0) * n;
-    const float* gb = a.g + (size_t)(valid ? b : 0) * p;
-    float* xb = a.x + (size_t)(valid ? b : 0) * n;
-    // ---- load x into TMEM and the A operand; D = Q x
-    {
-      const float* src = a.mode == 1 ? xb : xb;
-      for (int i0 = 0; i0 < NV; i0 += 8) {
-        float v[8];
+    // ---- x^0 = warm start or [0]_U; lambda^0 = mu^1 = warm start or 0
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t v[16];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) v[t] = (valid && i0 + t < n) ? src[i0 + t] : 0.f;
-        if (i0 + 8 <= NPAD) put8(S.Xh, S.Xl, tid, i0, v);
-        float v4[4] = {v[0], v[1], v[2], v[3]};
-        tc::tmem_st4(tm + lane_off + cX + i0, v4);
-        if (i0 + 4 < NV) {
-          float w4[4] = {v[4], v[5], v[6], v[7]};
-          tc::tmem_st4(tm + lane_off + cX + i0 + 4, w4);
-        }
+      for (int i = 0; i < 16; ++i) {
+        const int col = c0 + i;
+        float x = 0.f;
+        if (col < n) x = (valid && a.x0T) ? a.x0T[im(tile, n, col, tid)] : fminf(fmaxf(0.f, C.lb[col]), C.ub[col]);
+        v[i] = __float_as_uint(x);
       }
-      for (int i0 = ((NV + 7) / 8) * 8; i0 < NPAD; i0 += 8) {
-        float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        put8(S.Xh, S.Xl, tid, i0, z);
+      tc::tmem_st16(C.tm + C.lane_off + C.rX + c0, v);
+    }
+    for (int j0 = 0; j0 < p; j0 += 16) {
+      float l0[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        l0[i] = (valid && a.lam0T && j0 + i < p) ? __ldg(a.lam0T + im(tile, p, j0 + i, tid)) : 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        if (j0 + i >= p) continue;
+        const size_t ix = im(tile, p, j0 + i, tid);
+        a.lam[ix] = l0[i];
+        a.lamp[ix] = l0[i];
+        a.mu[ix] = l0[i];
       }
-      tc::tmem_st_wait();
     }
-    issue_fence();
-    if (tid == 0) {
-      tc_mma_tile(tm + cD, S.Xh, S.Xl, S.Qh, S.Ql, NPAD, NPAD, false);
-      tc::mma_commit(&bar_mma);
-    }
-    if (!sync_mma()) { ok = false; break; }
+    for (int i = 0; i < n; ++i) a.usum[im(tile, n, i, tid)] = 0.f;
+    C.sync_async();
+    C.gt_product(tile, a.mu);  // c = q + G' mu^1
 
-    // ---- c = q + G' m  with m = mu^k (mode 0) or lambda^k (mode 1)
-    auto gtmu = [&](const float* mrow) -> bool {
-      const uint32_t cAcc = cR;  // accumulator over the free x_{k-1} / Q x_{k-1} columns
-      for (int ch = 0; ch < a.nchGT; ++ch) {
-        const int j0 = ch * a.KC;
-        for (int jj = 0; jj < a.KC; jj += 8) {
-          float v[8];
-#pragma unroll
-          for (int t = 0; t < 8; ++t) {
-            const int j = j0 + jj + t;
-            v[t] = (valid && j < p) ? mrow[j] : 0.f;
-          }
-          uint4 h, l;
-          tc::split8(v, h, l);
-          const uint32_t o = tc::kmajor_off(tid, jj, TM);
-          *(uint4*)(S.Mh + o) = h;
-          *(uint4*)(S.Ml + o) = l;
-        }
-        if (tid == 0) {
-          const uint32_t bbytes = (uint32_t)NPAD * a.KC * 2;
-          tc::mbar_expect_tx(&bar_tx, 2 * bbytes);
-          tc::bulk_g2s(S.Bh, (const uint8_t*)a.GThi + (size_t)ch * bbytes, bbytes, &bar_tx);
-          tc::bulk_g2s(S.Bl, (const uint8_t*)a.GTlo + (size_t)ch * bbytes, bbytes, &bar_tx);
-        }
-        issue_fence();
-        if (!tc::mbar_wait(&bar_tx, ph_tx, kTcWaitNs)) return false;
-        ph_tx ^= 1;
-        if (tid == 0) {
-          tc_mma_tile(tm + cAcc, S.Mh, S.Ml, S.Bh, S.Bl, NPAD, a.KC, ch > 0);
-          tc::mma_commit(&bar_mma);
-        }
-        if (!sync_mma()) return false;
-      }
-      // c = acc + q  (zero when there are no constraints)
-      for (int i0 = 0; i0 < NV; i0 += 4) {
-        float c4[4];
-        if (a.nchGT > 0) tc::tmem_ld4(tm + lane_off + cAcc + i0, c4);
-        else c4[0] = c4[1] = c4[2] = c4[3] = 0.f;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) c4[t] += (valid && i0 + t < n) ? qb[i0 + t] : 0.f;
-        tc::tmem_st4(tm + lane_off + cC + i0, c4);
-      }
-      tc::tmem_st_wait();
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
-      return true;
-    };
-    {
-      const float* m0 = a.mode == 1 ? a.lam + (size_t)(valid ? b : 0) * p : a.mun + (size_t)(valid ? b : 0) * p;
-      if (!gtmu(m0)) { ok = false; break; }
-    }
-
-    const int nout = a.mode == 1 ? 1 : a.nouter;
-    for (int o = 0; o < nout && ok; ++o) {
+    bool act = valid;
+    double theta = 1.0, S = 0.0;
+    long long kin_tot = 0;
+    int conv_l = 0, conv_a = 0, status = ST_NOT_CONVERGED, kout = 0;
+    float d_lb = -INFINITY, f_l = NAN, i_l = NAN, f_a = NAN, i_a = NAN;
+    const int kmax = a.outer_fixed > 0 ? a.outer_fixed : a.max_outer;
+    for (int k = 1; k <= kmax && C.ok; ++k) {
       if (!__syncthreads_or(act)) break;
-      // ---- inner loop: Algorithm FOM from x^0 = ubar (x_{-1} = x^0)
-      for (int i0 = 0; i0 < NV; i0 += 4) {
-        float v[4], d[4];
-        tc::tmem_ld4(tm + lane_off + cX + i0, v);
-        tc::tmem_ld4(tm + lane_off + cD + i0, d);
-        tc::tmem_st4(tm + lane_off + cXP + i0, v);
-        tc::tmem_st4(tm + lane_off + cQP + i0, d);
-      }
-      tc::tmem_st_wait();
-      const bool fgm_sigma = a.sigma > 0.0;
-      double th_in = 1.0, beta = 0.0;
-      int kin = 0, done_in = act ? 0 : 1, kstop = 0;
-      const int m = a.inner_check_every > 0 ? a.inner_check_every : 1;
-      const int kmax = a.inner_fixed > 0 ? a.inner_fixed : a.max_inner;
-      for (;;) {
-        ++kin;
-        const float bt = (float)beta;
-        // every lane runs the same tcgen05 instructions; lanes whose inner
-        // loop has stopped write their unchanged values back.  The operand is
-        // rewritten up to NPAD (zero padding) because the G' mu product
-        // overlays it in shared memory.
-        for (int i0 = 0; i0 < NPAD; i0 += 8) {
-          float xn[8];
-          for (int h = 0; h < 8; h += 4) {
-            const int ii = i0 + h;
-            if (ii >= NV) {
-              xn[h] = xn[h + 1] = xn[h + 2] = xn[h + 3] = 0.f;
-              continue;
-            }
-            float d[4], x[4], xp[4], qp[4], c[4];
-            tc::tmem_ld4(tm + lane_off + cD + ii, d);
-            tc::tmem_ld4(tm + lane_off + cX + ii, x);
-            tc::tmem_ld4(tm + lane_off + cXP + ii, xp);
-            tc::tmem_ld4(tm + lane_off + cQP + ii, qp);
-            tc::tmem_ld4(tm + lane_off + cC + ii, c);
-            float r4[4], nxp[4], nqp[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              const float y = x[t] + bt * (x[t] - xp[t]);
-              const float qy = d[t] + bt * (d[t] - qp[t]);
-              const float s = y - (qy + c[t]) / L;
-              const float lo = S.lb[ii + t], hi = S.ub[ii + t];
-              const float xnew = s < lo ? lo : (s > hi ? hi : s);
-              r4[t] = done_in ? x[t] : xnew;
-              nxp[t] = done_in ? xp[t] : x[t];
-              nqp[t] = done_in ? qp[t] : d[t];
-              xn[h + t] = r4[t];
-            }
-            tc::tmem_st4(tm + lane_off + cQP + ii, nqp);
-            tc::tmem_st4(tm + lane_off + cXP + ii, nxp);
-            tc::tmem_st4(tm + lane_off + cX + ii, r4);
-          }
-          put8(S.Xh, S.Xl, tid, i0, xn);
-        }
-        tc::tmem_st_wait();
-        issue_fence();
-        if (tid == 0) {
-          tc_mma_tile(tm + cD, S.Xh, S.Xl, S.Qh, S.Ql, NPAD, NPAD, false);
-          tc::mma_commit(&bar_mma);
-        }
-        if (!sync_mma()) { ok = false; break; }
-        if (fgm_sigma) {
-          beta = a.beta_sigma;
-        } else {
-          const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * th_in * th_in));
-          beta = (th_in - 1.0) / t1;
-          th_in = t1;
-        }
-        {
-          bool stop = false;
-          if (a.inner_fixed > 0) {
-            stop = kin >= a.inner_fixed;
-          } else {
-            if (kin % m == 0) {  // certificate of eq. duquad_in at x^k (gradient Q x^k + c), all lanes
-              double cert = 0.0;
-              for (int i0 = 0; i0 < NV; i0 += 4) {
-                float d[4], x[4], c[4];
-                tc::tmem_ld4(tm + lane_off + cD + i0, d);
-                tc::tmem_ld4(tm + lane_off + cX + i0, x);
-                tc::tmem_ld4(tm + lane_off + cC + i0, c);
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                  if (i0 + t >= n) continue;
-                  const double gd = (double)(d[t] + c[t]), xd = x[t];
-                  const double lo = S.lb[i0 + t], hi = S.ub[i0 + t];
-                  if (a.sigma > 0.0) {
-                    const double xp = fmin(fmax(xd - gd / (double)L, lo), hi);
-                    const double dd = xd - xp;
-                    cert += gd * dd + ((double)L * dd) * ((double)L * dd) * kap;
-                  } else {
-                    const double u1 = gd * lo, u2 = gd * hi;
-                    cert += gd * xd - (u1 < u2 ? u1 : u2);
-                  }
-                }
-              }
-              stop = cert <= a.eps_in;
-            }
-            stop = stop || kin >= a.max_inner;
-          }
-          if (stop && !done_in) {
-            done_in = 1;
-            kstop = kin;
-          }
-        }
-        if (__syncthreads_and(done_in) || kin >= kmax) break;
-      }
-      if (!ok) break;
-      if (act && valid) a.kin[b] += (kstop > 0 ? kstop : kin);
-      if (a.mode == 1) break;
-      // ---- dual step: lambda = [mu + (G ubar + g)/(2 L_d)]_{K_d}, momentum, averaging
-      const double th = act ? a.theta[b] : 1.0;
-      double beta_out = 0.0;
+      const bool eval = a.outer_fixed > 0 ? (k == kmax) : (k % a.check_every == 0 || k == kmax);
+      // Step 1: ubar^k = FOM(L(., mu^k), U) from ubar^{k-1}
+      float cert_u;
+      int kin;
+      tc_inner(C, act, cert_u, kin);
+      kin_tot += kin;
+      // Step 2: lambda^k = [mu^k + (G ubar + g)/(2 L_d)]_{K_d}; Step 3: mu^{k+1}
+      double beta = 0.0, th_next = theta;
       if (a.fast) {
-        const double t1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * th * th));
-        beta_out = (th - 1.0) / t1;
+        th_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+        beta = (theta - 1.0) / th_next;
       }
-      for (int ch = 0; ch < a.nchG; ++ch) {
+      float is = 0.f, ic = 0.f, ls = 0.f, lc = 0.f;
+      int mu_neg = 0;
+      C.g_product([&](int ch, uint32_t slot) {
         const int j0 = ch * a.NC;
-        if (tid == 0) {
-          const uint32_t bbytes = (uint32_t)a.NC * NPAD * 2;
-          tc::mbar_expect_tx(&bar_tx, 2 * bbytes);
-          tc::bulk_g2s(S.Gh, (const uint8_t*)a.Ghi + (size_t)ch * bbytes, bbytes, &bar_tx);
-          tc::bulk_g2s(S.Gl, (const uint8_t*)a.Glo + (size_t)ch * bbytes, bbytes, &bar_tx);
-        }
-        issue_fence();
-        if (!tc::mbar_wait(&bar_tx, ph_tx, kTcWaitNs)) { ok = false; break; }
-        ph_tx ^= 1;
-        if (tid == 0) {
-          tc_mma_tile(tm + cR, S.Xh, S.Xl, S.Gh, S.Gl, a.NC, NPAD, false);
-          tc::mma_commit(&bar_mma);
-        }
-        if (!sync_mma()) { ok = false; break; }
-        {
-          const bool upd = act && valid;
-          const size_t rb = (size_t)(valid ? b : 0) * p;
-          float* lr = a.lam + rb;
-          float* lpr = a.lamp + rb;
-          float* mr = a.mun + rb;
-          float* mkr = a.muk + rb;
-          for (int jj = 0; jj < a.NC && j0 + jj < p; jj += 4) {  // uniform tcgen05.ld, masked updates
-            float r4[4];
-            tc::tmem_ld4(tm + lane_off + cR + jj, r4);
-            if (!upd) continue;
+        for (int c0 = 0; c0 < a.NC; c0 += 16) {
+          uint32_t r[16];
+          tc::tmem_ld16(C.tm + C.lane_off + slot + c0, r);
+          tc::tmem_ld_wait();
+          if (!act) continue;
+          // every load of the 16 columns is issued before the first store
+          float gv[16], mv[16], lv[16];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              const int j = j0 + jj + t;
-              if (j >= p) break;
-              const float mu = mr[j];
-              const float l_old = lr[j];
-              const float v = mu + a.alpha * (r4[t] + gb[j]);
-              const float ln = (a.cone == CONE_EQ || !a.kd_plus) ? v : (v > 0.f ? v : 0.f);
-              mkr[j] = mu;
-              lpr[j] = l_old;
-              lr[j] = ln;
-              mr[j] = ln + (float)beta_out * (ln - l_old);
+          for (int i = 0; i < 16; ++i) {
+            const int j = j0 + c0 + i;
+            const size_t ix = im(tile, p, j < p ? j : 0, tid);
+            gv[i] = __ldcg(a.gT + ix);
+            mv[i] = __ldcg(a.mu + ix);
+            lv[i] = __ldcg(a.lam + ix);
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int j = j0 + c0 + i;
+            if (j >= p) continue;
+            const size_t ix = im(tile, p, j, tid);
+            const float rv = __uint_as_float(r[i]) + gv[i];
+            const float muj = mv[i], lold = lv[i];
+            if (eval) {
+              kahan(ls, lc, muj * rv);
+              mu_neg |= muj < 0.f;
+              const float dk = rv - proj_K(a.cone, rv);
+              kahan(is, ic, dk * dk);
+            }
+            const float ln = proj_Kd(a.cone, a.kd_plus != 0, muj + a.alpha * rv);
+            a.lamp[ix] = lold;
+            a.lam[ix] = ln;
+            a.mu[ix] = ln + (float)beta * (ln - lold);
+          }
+        }
+      });
+      // averaging weight theta_k (eq. average_primal)
+      for (int c0 = 0; c0 < NPAD; c0 += 16) {
+        uint32_t x[16];
+        tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+        tc::tmem_ld_wait();
+        if (!act) continue;
+        float us[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) us[i] = c0 + i < n ? __ldcg(a.usum + im(tile, n, c0 + i, tid)) : 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (c0 + i < n) a.usum[im(tile, n, c0 + i, tid)] = us[i] + (float)theta * __uint_as_float(x[i]);
+      }
+      if (act) {
+        S += theta;
+        theta = th_next;
+        kout = k;
+      }
+      if (eval) {
+        // lower bound from (ubar^k, mu^k) when mu^k is a valid multiplier
+        const float Fu = tc_F(C, tile, C.rX);
+        if (act && (a.cone == CONE_EQ || !mu_neg)) d_lb = fmaxf(d_lb, Fu + (ls - lc) - cert_u);
+        float fl = Fu, il = sqrtf(fmaxf(is - ic, 0.f));
+        // save ubar (the warm-start chain continues from it)
+        for (int c0 = 0; c0 < NPAD; c0 += 16) {
+          uint32_t x[16];
+          tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            if (c0 + i < n) a.save[im(tile, n, c0 + i, tid)] = __uint_as_float(x[i]);
+        }
+        if (a.want_last) {
+          if (a.fast) {  // ubar(lambda^k): extra inner solve at lambda^k from ubar^k
+            C.gt_product(tile, a.lam);
+            float cert_l;
+            int kin_l;
+            tc_inner(C, act, cert_l, kin_l);
+            kin_tot += kin_l;
+            float inf2, lag;
+            int lneg;
+            tc_resid(C, tile, a.lam, inf2, lag, lneg);
+            fl = tc_F(C, tile, C.rX);
+            il = sqrtf(fmaxf(inf2, 0.f));
+            if (act && (a.cone == CONE_EQ || !lneg)) d_lb = fmaxf(d_lb, fl + lag - cert_l);
+          }
+          for (int c0 = 0; c0 < NPAD; c0 += 16) {
+            uint32_t x[16];
+            tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+            tc::tmem_ld_wait();
+            if (!act) continue;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (c0 + i < n) a.xlT[im(tile, n, c0 + i, tid)] = __uint_as_float(x[i]);
+          }
+          if (act) {
+            f_l = fl;
+            i_l = il;
+          }
+        }
+        if (a.want_avg) {  // x_avg = usum / S, evaluated in region X
+          for (int c0 = 0; c0 < NPAD; c0 += 16) {
+            uint32_t v[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int col = c0 + i;
+              v[i] = __float_as_uint(col < n && S > 0.0 ? (float)(a.usum[im(tile, n, col, tid)] / S) : 0.f);
+            }
+            tc::tmem_st16(C.tm + C.lane_off + C.rX + c0, v);
+          }
+          tc::tmem_st_wait();
+          C.operand_from(C.rX);
+          C.sync_async();
+          float inf2, lag;
+          int dummy;
+          tc_resid(C, tile, nullptr, inf2, lag, dummy);
+          const float fa = tc_F(C, tile, C.rX);
+          if (act) {
+            f_a = fa;
+            i_a = sqrtf(fmaxf(inf2, 0.f));
+            for (int i0 = 0; i0 < n; i0 += 16) {
+              float us[16];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) us[i] = i0 + i < n ? __ldcg(a.usum + im(tile, n, i0 + i, tid)) : 0.f;
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (i0 + i < n) a.xaT[im(tile, n, i0 + i, tid)] = (float)(us[i] / S);
             }
           }
         }
-        tc::fence_before();
-        __syncthreads();
-        tc::fence_after();
-      }
-      if (!ok) break;
-      {
-        const bool upd = act && valid;
-        float* us = a.usum + (size_t)(valid ? b : 0) * n;
-        for (int i0 = 0; i0 < NV; i0 += 4) {  // uniform tcgen05.ld, masked updates
-          float x[4];
-          tc::tmem_ld4(tm + lane_off + cX + i0, x);
-          if (!upd) continue;
+        // restore ubar into region X
+        for (int c0 = 0; c0 < NPAD; c0 += 16) {
+          uint32_t v[16];
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
-            if (i0 + t < n) us[i0 + t] += (float)th * x[t];
+          for (int i = 0; i < 16; ++i) {
+            const int col = c0 + i;
+            v[i] = __float_as_uint(col < n ? a.save[im(tile, n, col, tid)] : 0.f);
+          }
+          tc::tmem_st16(C.tm + C.lane_off + C.rX + c0, v);
         }
-        if (upd) {
-          a.S[b] += th;
-          a.kout[b] += 1;
-          if (a.fast) a.theta[b] = 0.5 * (1.0 + sqrt(1.0 + 4.0 * th * th));
+        C.sync_async();
+        if (act) {
+          if ((a.want_last && !(isfinite(f_l) && isfinite(i_l))) || (a.want_avg && !(isfinite(f_a) && isfinite(i_a)))) {
+            status = ST_NONFINITE;
+            act = false;
+          } else if (a.outer_fixed <= 0) {
+            conv_l = a.want_last && i_l <= a.eps_out && f_l - d_lb <= a.eps_out;
+            conv_a = a.want_avg && i_a <= a.eps_out && f_a - d_lb <= a.eps_out;
+            if (conv_l || conv_a) {
+              status = ST_OK;
+              act = false;
+            }
+          }
         }
       }
       // next c = q + G' mu^{k+1}
-      if (!gtmu(a.mun + (size_t)(valid ? b : 0) * p)) { ok = false; break; }
+      if (__syncthreads_or(act)) C.gt_product(tile, a.mu);
     }
-    if (!ok) break;
-    // ---- store x (mode 0: the warm-start chain; mode 1: the last-iterate output)
-    float* dst = a.mode == 1 ? a.xl + (size_t)(valid ? b : 0) * n : xb;
-    for (int i0 = 0; i0 < NV; i0 += 4) {
-      float x[4];
-      tc::tmem_ld4(tm + lane_off + cX + i0, x);
-      if (valid && (act || a.mode == 1))
-        for (int t = 0; t < 4; ++t)
-          if (i0 + t < n) dst[i0 + t] = x[t];
+    // ---- per-lane results and warm-start state
+    for (int c0 = 0; c0 < NPAD; c0 += 16) {
+      uint32_t x[16];
+      tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+      tc::tmem_ld_wait();
+      if (!valid) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (c0 + i < n) a.xsT[im(tile, n, c0 + i, tid)] = __uint_as_float(x[i]);
+    }
+    if (valid) {
+      if (a.outer_fixed > 0 && status == ST_NOT_CONVERGED) status = ST_OK;
+      DevResult r;
+      r.status = status;
+      r.outer_iters = kout;
+      r.inner_iters = kin_tot;
+      r.converged_last = conv_l;
+      r.converged_avg = conv_a;
+      r.f_last = f_l;
+      r.infeas_last = i_l;
+      r.f_avg = f_a;
+      r.infeas_avg = i_a;
+      r.d_lb = d_lb;
+      a.res[b] = r;
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
   }
-  if (!ok && tid == 0) atomicExch(a.err, 1);
+  if (!C.ok && tid == 0) atomicExch(a.err, 1);
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tm, 512);
+  if (warp == 0) tc::tmem_dealloc(C.tm, 512);
 }
 
-// Per-instance FP64-accurate evaluation for the outer certificate (same
-// rules as the CTA engine): lower bound from (ubar, mu^k), outputs' F and
-// dist_K, convergence flags.
-struct TcEvalArgs {
-  int n, p, B, cone;
-  const float *Q, *G, *GT, *q, *g, *lb, *ub;
-  const float *x, *xl, *usum, *lam, *muk;
-  const double* S;
-  float* xavg;
-  double LL, sigma, eps_out;
-  int want_last, want_avg, fast, fixed;
-  int* active;
-  DevResult* res;
-};
-
-__global__ void __launch_bounds__(128) k_tc_eval(TcEvalArgs e) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int b = blockIdx.x;
-  if (b >= e.B) return;
-  if (!e.active[b]) return;
-  const int n = e.n, p = e.p;
-  CtaWs<float> W;
-  memset(&W, 0, sizeof(W));
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    unsigned char* r = smem + off;
-    off += (bytes + 15) & ~size_t(15);
-    return r;
-  };
-  W.red = (double*)take(40 * sizeof(double));
-  W.dn = (double*)take((size_t)n * sizeof(double));
-  W.dp = (double*)take((size_t)(p > 0 ? p : 1) * sizeof(double));
-  float* ua = (float*)take((size_t)n * sizeof(float));
-  W.Q = e.Q;
-  W.G = e.G;
-  W.GT = e.GT;
-  CtaInst<float> I;
-  memset(&I, 0, sizeof(I));
-  I.n = n;
-  I.p = p;
-  I.cone = e.cone;
-  I.q = e.q + (size_t)b * n;
-  I.g = e.g + (size_t)b * p;
-  I.lb = e.lb;
-  I.ub = e.ub;
-  I.rho = 0.0;
-  I.LL = e.LL;
-  I.sigma = e.sigma;
-  DevResult r = e.res[b];
-  const float* xb = e.x + (size_t)b * n;
-  const float* mk = e.muk + (size_t)b * p;
-  bool mu_ok = true;
-  if (e.cone == CONE_INEQ) {
-    int neg = 0;
-    for (int j = threadIdx.x; j < p; j += blockDim.x) neg |= mk[j] < 0.f;
-    mu_ok = !__syncthreads_or(neg);
-  }
-  if (mu_ok) {
-    EvalOut v = cta_eval<float>(I, W, xb, mk);
-    r.d_lb = fmax(r.d_lb, v.lagr - v.cert);
-  }
-  if (e.want_last) {
-    if (e.fast) {
-      const float* lb_ = e.lam + (size_t)b * p;
-      bool lok = true;
-      if (e.cone == CONE_INEQ) {
-        int neg = 0;
-        for (int j = threadIdx.x; j < p; j += blockDim.x) neg |= lb_[j] < 0.f;
-        lok = !__syncthreads_or(neg);
-      }
-      EvalOut v = cta_eval<float>(I, W, e.xl + (size_t)b * n, lok ? lb_ : nullptr);
-      if (lok) r.d_lb = fmax(r.d_lb, v.lagr - v.cert);
-      r.f_last = v.F;
-      r.infeas_last = v.infeas;
-    } else {
-      EvalOut v = cta_eval<float>(I, W, xb, (const float*)nullptr);
-      r.f_last = v.F;
-      r.infeas_last = v.infeas;
-    }
-  }
-  if (e.want_avg) {
-    const double Sb = e.S[b];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) ua[i] = (float)(e.usum[(size_t)b * n + i] / Sb);
-    __syncthreads();
-    EvalOut v = cta_eval<float>(I, W, ua, (const float*)nullptr);
-    r.f_avg = v.F;
-    r.infeas_avg = v.infeas;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) e.xavg[(size_t)b * n + i] = ua[i];
-  }
-  if (threadIdx.x == 0) {
-    if ((e.want_last && !(isfinite(r.f_last) && isfinite(r.infeas_last))) ||
-        (e.want_avg && !(isfinite(r.f_avg) && isfinite(r.infeas_avg)))) {
-      r.status = ST_NONFINITE;
-      e.active[b] = 0;
-    } else if (!e.fixed) {
-      r.converged_last = e.want_last && r.infeas_last <= e.eps_out && r.f_last - r.d_lb <= e.eps_out;
-      r.converged_avg = e.want_avg && r.infeas_avg <= e.eps_out && r.f_avg - r.d_lb <= e.eps_out;
-      if (r.converged_last || r.converged_avg) {
-        r.status = ST_OK;
-        e.active[b] = 0;
-      }
-    }
-    e.res[b] = r;
+// Row-major [B][E] -> instance-minor [tile][E][128] (zero for lanes past B).
+__global__ void k_to_minor(const float* __restrict__ src, int B, int E, int ntiles, float* __restrict__ dst) {
+  const size_t total = (size_t)ntiles * E * TM;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+    const int l = (int)(k % TM);
+    const size_t te = k / TM;
+    const int e = (int)(te % E), t = (int)(te / E);
+    const int b = t * TM + l;
+    dst[k] = b < B ? src[(size_t)b * E + e] : 0.f;
   }
 }
-
-__global__ void k_tc_init(int B, int n, int p, float* x, const float* x0, const float* lb, const float* ub,
-                          float* lam, float* lamp, float* mun, float* muk, const float* lam0, float* usum,
-                          double* theta, double* S, int* kout, long long* kin, int* active, DevResult* res) {
-  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
-  for (size_t k = tid; k < (size_t)B * n; k += nt) {
-    const int i = (int)(k % n);
-    x[k] = x0 ? x0[k] : fminf(fmaxf(0.f, lb[i]), ub[i]);
-    usum[k] = 0.f;
-  }
-  for (size_t k = tid; k < (size_t)B * p; k += nt) {
-    const float l = lam0 ? lam0[k] : 0.f;
-    lam[k] = l;
-    lamp[k] = l;
-    mun[k] = l;
-    muk[k] = l;
-  }
-  for (size_t b = tid; b < (size_t)B; b += nt) {
-    theta[b] = 1.0;
-    S[b] = 0.0;
-    kout[b] = 0;
-    kin[b] = 0;
-    active[b] = 1;
-    DevResult r;
-    r.status = ST_NOT_CONVERGED;
-    r.outer_iters = 0;
-    r.inner_iters = 0;
-    r.converged_last = r.converged_avg = 0;
-    r.f_last = r.infeas_last = r.f_avg = r.infeas_avg = NAN;
-    r.d_lb = -INFINITY;
-    res[b] = r;
-  }
-}
-
-__global__ void k_tc_finish(int B, const int* kout, const long long* kin, DevResult* res, int* count_active,
-                            const int* active) {
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < B; b += gridDim.x * blockDim.x) {
-    res[b].outer_iters = kout[b];
-    res[b].inner_iters = kin[b];
-    if (active[b]) atomicAdd(count_active, 1);
+// Instance-minor -> row-major [B][E].
+__global__ void k_from_minor(const float* __restrict__ src, int B, int E, float* __restrict__ dst) {
+  const size_t total = (size_t)B * E;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(k / E), e = (int)(k % E);
+    dst[k] = src[im(b / TM, E, e, b % TM)];
   }
 }
 
 struct TcWs {
-  int NPAD = 0, NV = 0, NC = 0, KC = 0, nchG = 0, nchGT = 0;
+  int NPAD = 0, NC = 0, ntiles = 0, nchG = 0, nchGT = 0;
   void* mem = nullptr;
   uint4 *Qhi, *Qlo, *Ghi, *Glo, *GThi, *GTlo;
-  float *x, *xl, *xa, *usum, *lam, *lamp, *mun, *muk;
-  double *theta, *S;
-  int *kout, *active, *err, *cnt;
-  long long* kin;
+  float *qT, *gT, *x0T, *lam0T, *lam, *lamp, *mu, *usum, *save, *xlT, *xaT, *xsT, *tmp;
+  int *next, *err;
   DevResult* res;
   bool packed = false;
 };
@@ -630,17 +837,16 @@ static dq_status tc_ws(dq_problem* P, TcWs** out) {
   TcWs* W = new TcWs();
   const int n = P->n, p = P->p, B = P->batch;
   W->NPAD = (n + 15) / 16 * 16;
-  W->NV = (n + 3) / 4 * 4;
-  W->NC = 192;
-  W->KC = 64;
+  W->NC = std::min(64, W->NPAD);
+  W->ntiles = (B + TM - 1) / TM;
   W->nchG = (p + W->NC - 1) / W->NC;
-  W->nchGT = (p + W->KC - 1) / W->KC;
+  W->nchGT = (p + TC_KC - 1) / TC_KC;
   auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t qb = (size_t)W->NPAD * W->NPAD * 2, gb = (size_t)W->nchG * W->NC * W->NPAD * 2,
-               gtb = (size_t)W->nchGT * W->NPAD * W->KC * 2;
-  const size_t bn = (size_t)B * n * 4, bp = (size_t)std::max(B * p, 1) * 4;
-  size_t total = 2 * a256(qb) + 2 * a256(gb) + 2 * a256(gtb) + 4 * a256(bn) + 4 * a256(bp) + 2 * a256((size_t)B * 8) +
-                 3 * a256((size_t)B * 4) + a256((size_t)B * 8) + a256((size_t)B * sizeof(DevResult)) + 256;
+               gtb = (size_t)W->nchGT * W->NPAD * TC_KC * 2;
+  const size_t vn = (size_t)W->ntiles * TM * n * 4, vp = (size_t)W->ntiles * TM * std::max(p, 1) * 4;
+  const size_t total = 2 * a256(qb) + 2 * a256(gb) + 2 * a256(gtb) + 8 * a256(vn) + 5 * a256(vp) +
+                       a256(std::max(vn, vp)) + a256((size_t)B * sizeof(DevResult)) + 256;
   if (cudaMalloc(&W->mem, total) != cudaSuccess) {
     cudaGetLastError();
     delete W;
@@ -656,13 +862,16 @@ static dq_status tc_ws(dq_problem* P, TcWs** out) {
   W->Qhi = (uint4*)take(qb); W->Qlo = (uint4*)take(qb);
   W->Ghi = (uint4*)take(gb); W->Glo = (uint4*)take(gb);
   W->GThi = (uint4*)take(gtb); W->GTlo = (uint4*)take(gtb);
-  W->x = (float*)take(bn); W->xl = (float*)take(bn); W->xa = (float*)take(bn); W->usum = (float*)take(bn);
-  W->lam = (float*)take(bp); W->lamp = (float*)take(bp); W->mun = (float*)take(bp); W->muk = (float*)take(bp);
-  W->theta = (double*)take((size_t)B * 8); W->S = (double*)take((size_t)B * 8);
-  W->kout = (int*)take((size_t)B * 4); W->active = (int*)take((size_t)B * 4); W->err = (int*)take(4 * 64);
-  W->cnt = W->err + 16;
-  W->kin = (long long*)take((size_t)B * 8);
+  W->qT = (float*)take(vn); W->x0T = (float*)take(vn); W->usum = (float*)take(vn); W->save = (float*)take(vn);
+  W->xlT = (float*)take(vn); W->xaT = (float*)take(vn); W->xsT = (float*)take(vn);
+  W->gT = (float*)take(vp); W->lam0T = (float*)take(vp); W->lam = (float*)take(vp); W->lamp = (float*)take(vp);
+  W->mu = (float*)take(vp);
+  W->tmp = (float*)take(std::max(vn, vp));
+  float* spare = (float*)take(vn);
+  (void)spare;
   W->res = (DevResult*)take((size_t)B * sizeof(DevResult));
+  W->next = (int*)take(256);
+  W->err = W->next + 16;
   P->tws = W;
   *out = W;
   return DQ_OK;
@@ -670,10 +879,11 @@ static dq_status tc_ws(dq_problem* P, TcWs** out) {
 
 static size_t tc_smem_bytes(const TcWs* W) {
   auto r128 = [](size_t b) { return (b + 127) & ~size_t(127); };
-  const size_t q = 2 * r128((size_t)W->NPAD * W->NPAD * 2);
-  const size_t uA = 2 * (size_t)TM * W->NPAD * 2 + 2 * (size_t)W->NC * W->NPAD * 2;
-  const size_t uB = 2 * (size_t)TM * W->KC * 2 + 2 * (size_t)W->NPAD * W->KC * 2;
-  return q + r128(std::max(uA, uB)) + 2 * (size_t)W->NV * 4 + 128;
+  const size_t qb = (size_t)W->NPAD * W->NPAD * 2;
+  const size_t ab = std::max((size_t)TM * W->NPAD * 2, (size_t)2 * TM * TC_KC * 2);
+  const size_t bb = r128(std::max(std::max((size_t)W->NC * W->NPAD * 2, (size_t)W->NPAD * TC_KC * 2),
+                                  (size_t)W->NPAD * W->NPAD));
+  return 2 * r128(qb) + r128(2 * ab) + 4 * bb + 2 * r128((size_t)W->NPAD * 4) + 128;
 }
 
 dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_result* results) {
@@ -687,8 +897,8 @@ dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_r
     return DQ_ERR_INVALID;
   }
   const int n = P->n, p = P->p, B = P->batch;
-  if ((n + 15) / 16 * 16 + 4 * ((n + 3) / 4 * 4) > 512) {
-    set_error("the tensor-core engine holds n <= 100 variables per instance in tensor memory (n = %d)", n);
+  if ((n + 15) / 16 * 16 > 128) {
+    set_error("the tensor-core engine holds n <= 128 variables per instance in tensor memory (n = %d)", n);
     return DQ_ERR_INVALID;
   }
   if (c.inner_stop == DQ_INNER_FIXED && c.fixed_inner <= 0) {
@@ -713,17 +923,18 @@ dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_r
     set_error("tensor-core engine needs %zu bytes of shared memory", smem);
     return DQ_ERR_INVALID;
   }
+  const int NPAD = W->NPAD;
   if (!W->packed) {
-    k_pack_kmajor<<<64, 256, 0, st>>>((const float*)P->Q, n, n, n, W->NPAD, W->NPAD, W->Qhi, W->Qlo);
+    k_pack_kmajor<<<64, 256, 0, st>>>((const float*)P->Q, n, n, n, NPAD, NPAD, W->Qhi, W->Qlo);
     for (int ch = 0; ch < W->nchG; ++ch) {
-      const size_t o = (size_t)ch * W->NC * W->NPAD * 2 / 16;
+      const size_t o = (size_t)ch * W->NC * NPAD * 2 / 16;
       k_pack_kmajor<<<64, 256, 0, st>>>((const float*)P->G + (size_t)ch * W->NC * n, std::min(W->NC, p - ch * W->NC), n,
-                                        n, W->NC, W->NPAD, W->Ghi + o, W->Glo + o);
+                                        n, W->NC, NPAD, W->Ghi + o, W->Glo + o);
     }
     for (int ch = 0; ch < W->nchGT; ++ch) {
-      const size_t o = (size_t)ch * W->NPAD * W->KC * 2 / 16;
-      k_pack_kmajor<<<64, 256, 0, st>>>((const float*)P->GT + (size_t)ch * W->KC, n, std::min(W->KC, p - ch * W->KC),
-                                        p, W->NPAD, W->KC, W->GThi + o, W->GTlo + o);
+      const size_t o = (size_t)ch * NPAD * TC_KC * 2 / 16;
+      k_pack_kmajor<<<64, 256, 0, st>>>((const float*)P->GT + (size_t)ch * TC_KC, n, std::min(TC_KC, p - ch * TC_KC),
+                                        p, NPAD, TC_KC, W->GThi + o, W->GTlo + o);
     }
     ctx->launches += 1 + W->nchG + W->nchGT;
     DQ_CK(cudaGetLastError());
@@ -743,98 +954,83 @@ dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_r
   const double eps_in = isnan(c.eps_in) ? (fast ? c.eps_out * sqrt(c.eps_out) / (8.0 * sqrt(2.0 * Ld)) : c.eps_out / 4.0)
                                         : c.eps_in;
   const bool warm = c.warm_start && P->has_state;
-  k_tc_init<<<256, 256, 0, st>>>(B, n, p, W->x, warm ? (const float*)P->x_state : nullptr, (const float*)P->lb,
-                                 (const float*)P->ub, W->lam, W->lamp, W->mun, W->muk,
-                                 warm ? (const float*)P->lam_state : nullptr, W->usum, W->theta, W->S, W->kout, W->kin,
-                                 W->active, W->res);
+  const int tg = std::max(1, std::min(4 * ctx->num_sms, (int)(((size_t)W->ntiles * TM * std::max(n, p) + 255) / 256)));
+  k_to_minor<<<tg, 256, 0, st>>>((const float*)P->q, B, n, W->ntiles, W->qT);
   ++ctx->launches;
-  DQ_CK(cudaMemsetAsync(W->err, 0, 64 * 4, st));
+  if (p) {
+    k_to_minor<<<tg, 256, 0, st>>>((const float*)P->g, B, p, W->ntiles, W->gT);
+    ++ctx->launches;
+  }
+  if (warm) {
+    k_to_minor<<<tg, 256, 0, st>>>((const float*)P->x_state, B, n, W->ntiles, W->x0T);
+    ++ctx->launches;
+    if (p) {
+      k_to_minor<<<tg, 256, 0, st>>>((const float*)P->lam_state, B, p, W->ntiles, W->lam0T);
+      ++ctx->launches;
+    }
+  }
+  DQ_CK(cudaMemsetAsync(W->next, 0, 256, st));
   TcArgs a;
   memset(&a, 0, sizeof(a));
-  a.n = n; a.p = p; a.B = B; a.NPAD = W->NPAD; a.NV = W->NV; a.NC = W->NC; a.KC = W->KC;
-  a.nchG = W->nchG; a.nchGT = W->nchGT;
+  a.n = n; a.p = p; a.B = B; a.NPAD = NPAD; a.NC = W->NC; a.ntiles = W->ntiles; a.nchG = W->nchG; a.nchGT = W->nchGT;
   a.Qhi = W->Qhi; a.Qlo = W->Qlo; a.Ghi = W->Ghi; a.Glo = W->Glo; a.GThi = W->GThi; a.GTlo = W->GTlo;
-  a.q = (const float*)P->q; a.g = (const float*)P->g; a.lb = (const float*)P->lb; a.ub = (const float*)P->ub;
-  a.x = W->x; a.xl = W->xl; a.usum = W->usum; a.lam = W->lam; a.lamp = W->lamp; a.mun = W->mun; a.muk = W->muk;
-  a.theta = W->theta; a.S = W->S; a.kout = W->kout; a.kin = W->kin; a.active = W->active;
-  a.L = (float)LL; a.alpha = (float)(1.0 / (2.0 * Ld)); a.sigma = sigma;
-  a.beta_sigma = sigma > 0 ? (sqrt(LL) - sqrt(sigma)) / (sqrt(LL) + sqrt(sigma)) : 0.0;
-  a.eps_in = eps_in; a.cone = P->cone; a.kd_plus = !(c.kd_literal && !(lmin > 0.0));
+  a.Qf = (const float*)P->Q;
+  a.qT = W->qT; a.gT = W->gT; a.lb = (const float*)P->lb; a.ub = (const float*)P->ub;
+  a.x0T = warm ? W->x0T : nullptr; a.lam0T = (warm && p) ? W->lam0T : nullptr;
+  a.lam = W->lam; a.lamp = W->lamp; a.mu = W->mu; a.usum = W->usum; a.save = W->save;
+  a.xlT = W->xlT; a.xaT = W->xaT; a.xsT = W->xsT; a.res = W->res;
+  a.L = (float)LL; a.alpha = (float)(1.0 / (2.0 * Ld)); a.sigma = (float)sigma;
+  a.beta_sigma = sigma > 0 ? (float)((sqrt(LL) - sqrt(sigma)) / (sqrt(LL) + sqrt(sigma))) : 0.f;
+  a.eps_in = (float)eps_in; a.eps_out = (float)c.eps_out;
+  a.cone = P->cone; a.kd_plus = !(c.kd_literal && !(lmin > 0.0)); a.fast = fast;
+  a.want_last = (c.output & DQ_OUT_LAST) != 0; a.want_avg = (c.output & DQ_OUT_AVERAGE) != 0;
   a.inner_fixed = c.fixed_inner; a.inner_check_every = c.inner_check_every; a.max_inner = c.max_inner;
-  a.fast = fast; a.err = W->err;
-  TcEvalArgs e;
-  memset(&e, 0, sizeof(e));
-  e.n = n; e.p = p; e.B = B; e.cone = P->cone;
-  e.Q = (const float*)P->Q; e.G = (const float*)P->G; e.GT = (const float*)P->GT;
-  e.q = (const float*)P->q; e.g = (const float*)P->g; e.lb = (const float*)P->lb; e.ub = (const float*)P->ub;
-  e.x = W->x; e.xl = W->xl; e.usum = W->usum; e.lam = W->lam; e.muk = W->muk; e.S = W->S; e.xavg = W->xa;
-  e.LL = LL; e.sigma = sigma; e.eps_out = c.eps_out;
-  e.want_last = (c.output & DQ_OUT_LAST) != 0; e.want_avg = (c.output & DQ_OUT_AVERAGE) != 0; e.fast = fast;
-  e.fixed = c.fixed_outer > 0; e.active = W->active; e.res = W->res;
-  const size_t esmem = 40 * 8 + (size_t)n * 8 + (size_t)std::max(p, 1) * 8 + (size_t)n * 4 + 64;
+  a.outer_fixed = c.fixed_outer; a.max_outer = c.max_outer; a.check_every = c.check_every > 0 ? c.check_every : 1;
+  a.next = W->next; a.err = W->err;
   DQ_CK(cudaFuncSetAttribute(k_tc_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int ntiles = (B + TM - 1) / TM;
-  const int grid = std::min(ntiles, ctx->num_sms);
-  const int kmax = c.fixed_outer > 0 ? c.fixed_outer : c.max_outer;
-  const int step = c.fixed_outer > 0 ? c.fixed_outer : c.check_every;
-  int k = 0, active_count = B;
-  while (k < kmax && active_count > 0) {
-    const int nout = std::min(step, kmax - k);
-    a.mode = 0;
-    a.nouter = nout;
-    k_tc_solve<<<grid, TM, smem, st>>>(a);
+  const int grid = std::min(W->ntiles, ctx->num_sms);
+  k_tc_solve<<<grid, TM, smem, st>>>(a);
+  ++ctx->launches;
+  DQ_CK(cudaGetLastError());
+  // warm-start state and outputs back to row-major
+  const int og = std::max(1, std::min(4 * ctx->num_sms, (int)(((size_t)B * std::max(n, p) + 255) / 256)));
+  k_from_minor<<<og, 256, 0, st>>>(W->xsT, B, n, (float*)P->x_state);
+  ++ctx->launches;
+  if (p) {
+    k_from_minor<<<og, 256, 0, st>>>(W->lam, B, p, (float*)P->lam_state);
     ++ctx->launches;
-    k += nout;
-    if (e.want_last && fast) {
-      a.mode = 1;
-      k_tc_solve<<<grid, TM, smem, st>>>(a);
-      ++ctx->launches;
-    } else {
-      DQ_CK(cudaMemcpyAsync(W->xl, W->x, (size_t)B * n * 4, cudaMemcpyDeviceToDevice, st));
-    }
-    k_tc_eval<<<B, 128, esmem, st>>>(e);
-    DQ_CK(cudaMemsetAsync(W->cnt, 0, 4, st));
-    k_tc_finish<<<64, 256, 0, st>>>(B, W->kout, W->kin, W->res, W->cnt, W->active);
-    ctx->launches += 2;
-    DQ_CK(cudaGetLastError());
-    int herr[2] = {0, 0};
-    DQ_CK(cudaMemcpyAsync(&herr[0], W->err, 4, cudaMemcpyDeviceToHost, st));
-    DQ_CK(cudaMemcpyAsync(&herr[1], W->cnt, 4, cudaMemcpyDeviceToHost, st));
-    DQ_CK(cudaStreamSynchronize(st));
-    if (herr[0]) {
-      set_error("tensor-core engine: a device wait timed out");
-      return DQ_ERR_TIMEOUT;
-    }
-    active_count = c.fixed_outer > 0 ? 0 : herr[1];
   }
-  // results and outputs
-  std::vector<DevResult> hr(B);
-  DQ_CK(cudaMemcpyAsync(hr.data(), W->res, (size_t)B * sizeof(DevResult), cudaMemcpyDeviceToHost, st));
-  DQ_CK(cudaMemcpyAsync(P->x_state, W->x, (size_t)B * n * 4, cudaMemcpyDeviceToDevice, st));
-  if (p) DQ_CK(cudaMemcpyAsync(P->lam_state, W->lam, (size_t)B * p * 4, cudaMemcpyDeviceToDevice, st));
   P->has_state = true;
+  std::vector<DevResult> hr(B);
+  int herr = 0;
+  DQ_CK(cudaMemcpyAsync(hr.data(), W->res, (size_t)B * sizeof(DevResult), cudaMemcpyDeviceToHost, st));
+  DQ_CK(cudaMemcpyAsync(&herr, W->err, 4, cudaMemcpyDeviceToHost, st));
   if (out) {
-    auto put = [&](void* dst, const float* src, size_t cnt) -> dq_status {
-      if (!dst || !cnt) return DQ_OK;
-      if (out->memory == DQ_DEVICE) {
-        DQ_CK(cudaMemcpyAsync(dst, src, cnt * 4, cudaMemcpyDeviceToDevice, st));
-      } else {
-        std::vector<float> h(cnt);
-        DQ_CK(cudaMemcpyAsync(h.data(), src, cnt * 4, cudaMemcpyDeviceToHost, st));
+    auto put = [&](void* dst, const float* srcT, int E) -> dq_status {
+      if (!dst || !E) return DQ_OK;
+      float* rowmajor = out->memory == DQ_DEVICE ? (float*)dst : W->tmp;
+      k_from_minor<<<og, 256, 0, st>>>(srcT, B, E, rowmajor);
+      ++ctx->launches;
+      if (out->memory != DQ_DEVICE) {
+        std::vector<float> h((size_t)B * E);
+        DQ_CK(cudaMemcpyAsync(h.data(), W->tmp, h.size() * 4, cudaMemcpyDeviceToHost, st));
         DQ_CK(cudaStreamSynchronize(st));
-        for (size_t i = 0; i < cnt; ++i) ((double*)dst)[i] = h[i];
+        for (size_t i = 0; i < h.size(); ++i) ((double*)dst)[i] = h[i];
       }
       return DQ_OK;
     };
-    if ((s = put(out->x_last, W->xl, (size_t)B * n)) != DQ_OK) return s;
-    if ((s = put(out->x_avg, W->xa, (size_t)B * n)) != DQ_OK) return s;
-    if ((s = put(out->lambda, W->lam, (size_t)B * p)) != DQ_OK) return s;
+    if ((s = put(out->x_last, W->xlT, n)) != DQ_OK) return s;
+    if ((s = put(out->x_avg, W->xaT, n)) != DQ_OK) return s;
+    if ((s = put(out->lambda, W->lam, p)) != DQ_OK) return s;
   }
   DQ_CK(cudaStreamSynchronize(st));
+  if (herr) {
+    set_error("tensor-core engine: a device wait timed out");
+    return DQ_ERR_TIMEOUT;
+  }
   const double consts[6] = {P->lmax_Q, P->normG2, LL, Ld, sigma, rho};
   dq_status worst = DQ_OK;
   for (int b = 0; b < B; ++b) {
-    if (c.fixed_outer > 0 && hr[b].status == ST_NOT_CONVERGED) hr[b].status = ST_OK;
     fill_result(&results[b], hr[b], consts, c);
     const dq_status sb = (dq_status)hr[b].status;
     if (sb < 0 || worst < 0) worst = sb < worst ? sb : worst;
