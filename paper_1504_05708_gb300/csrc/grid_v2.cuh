@@ -201,24 +201,33 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
             const int s = (int)(gc % V2_STAGES);
             ok = tc::mbar_wait(&full[s], (gc / V2_STAGES) & 1, V2_WAIT_NS) && ok;
             const float4* ch = ring + (size_t)s * V2_CH4;  // column c4 at ch[c4 - k * V2_CH4]
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int m = 2 * k + h, c4 = t + V2_CONS * m;
-              if (c4 >= f0 && c4 < n4) {
-                const float4 v = ch[c4 - k * V2_CH4];
-                float d = v.x * xr[m].x;
-                d = fmaf(v.y, xr[m].y, d);
-                d = fmaf(v.z, xr[m].z, d);
-                d = fmaf(v.w, xr[m].w, d);
-                const float yk = d - comp, tk = sa + yk;  // Kahan pair
-                comp = (tk - sa) - yk;
-                sa = tk;
-                part[m].x = fmaf(xi, v.x, part[m].x);
-                part[m].y = fmaf(xi, v.y, part[m].y);
-                part[m].z = fmaf(xi, v.z, part[m].z);
-                part[m].w = fmaf(xi, v.w, part[m].w);
-              }
+            // both of this thread's float4 of the chunk are loaded before use; their dots are
+            // independent chains, and one Kahan step per chunk adds them to the row dot
+            const int m0 = 2 * k, c40 = t + V2_CONS * m0, c41 = c40 + V2_CONS;
+            const bool in0 = c40 >= f0 && c40 < n4, in1 = c41 >= f0 && c41 < n4;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 v0 = in0 ? ch[c40 - k * V2_CH4] : z4;
+            const float4 v1 = in1 ? ch[c41 - k * V2_CH4] : z4;
+            float d0 = v0.x * xr[m0].x, d1 = v1.x * xr[m0 + 1].x;
+            d0 = fmaf(v0.y, xr[m0].y, d0);
+            d1 = fmaf(v1.y, xr[m0 + 1].y, d1);
+            d0 = fmaf(v0.z, xr[m0].z, d0);
+            d1 = fmaf(v1.z, xr[m0 + 1].z, d1);
+            d0 = fmaf(v0.w, xr[m0].w, d0);
+            d1 = fmaf(v1.w, xr[m0 + 1].w, d1);
+            {
+              const float yk = (d0 + d1) - comp, tk = sa + yk;  // Kahan pair
+              comp = (tk - sa) - yk;
+              sa = tk;
             }
+            part[m0].x = fmaf(xi, v0.x, part[m0].x);
+            part[m0].y = fmaf(xi, v0.y, part[m0].y);
+            part[m0].z = fmaf(xi, v0.z, part[m0].z);
+            part[m0].w = fmaf(xi, v0.w, part[m0].w);
+            part[m0 + 1].x = fmaf(xi, v1.x, part[m0 + 1].x);
+            part[m0 + 1].y = fmaf(xi, v1.y, part[m0 + 1].y);
+            part[m0 + 1].z = fmaf(xi, v1.z, part[m0 + 1].z);
+            part[m0 + 1].w = fmaf(xi, v1.w, part[m0 + 1].w);
             release(gc);
             ++gc;
           }
@@ -249,20 +258,20 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
           const int s = (int)(gk % V2_STAGES);
           ok = tc::mbar_wait(&full[s], (gk / V2_STAGES) & 1, V2_WAIT_NS) && ok;
           const float4* ch = ring + (size_t)s * V2_CH4;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int m = 2 * k + h, c4 = t + V2_CONS * m;
-            if (c4 < n4) {
-              const float4 v = ch[c4 - k * V2_CH4];
-              float d = v.x * xr[m].x;
-              d = fmaf(v.y, xr[m].y, d);
-              d = fmaf(v.z, xr[m].z, d);
-              d = fmaf(v.w, xr[m].w, d);
-              const float yk = d - comp, tk = sa + yk;
-              comp = (tk - sa) - yk;
-              sa = tk;
-            }
-          }
+          const int m0 = 2 * k, c40 = t + V2_CONS * m0, c41 = c40 + V2_CONS;
+          const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 v0 = c40 < n4 ? ch[c40 - k * V2_CH4] : z4;
+          const float4 v1 = c41 < n4 ? ch[c41 - k * V2_CH4] : z4;
+          float d0 = v0.x * xr[m0].x, d1 = v1.x * xr[m0 + 1].x;
+          d0 = fmaf(v0.y, xr[m0].y, d0);
+          d1 = fmaf(v1.y, xr[m0 + 1].y, d1);
+          d0 = fmaf(v0.z, xr[m0].z, d0);
+          d1 = fmaf(v1.z, xr[m0 + 1].z, d1);
+          d0 = fmaf(v0.w, xr[m0].w, d0);
+          d1 = fmaf(v1.w, xr[m0 + 1].w, d1);
+          const float yk = (d0 + d1) - comp, tk = sa + yk;
+          comp = (tk - sa) - yk;
+          sa = tk;
         }
       }
       // one barrier per row: the 16 warp sums go to a buffer that alternates

@@ -124,3 +124,64 @@ def test_single_pass_matches_two_pass(ctx, alg, monkeypatch):
     ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, inner_fixed=7, outer_fixed=3)
     assert rel(x2, x1) <= 2e-5 and rel(a2, a1) <= 2e-5
     assert rel(x2, ro.x_last) <= 1e-4 and rel(x1, ro.x_last) <= 1e-4
+
+
+def _eq_qp(inst):
+    return O.QP(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, cone=O.CONE_EQ)
+
+
+def _eq_constants(inst, alg):
+    return O.constants(_eq_qp(inst), ALG_IDS[alg], lmin_Q=inst.lmin_Q)
+
+
+@pytest.mark.parametrize("alg", ["ADGM", "ADFGM"])
+@pytest.mark.parametrize("n,p", [(301, 120), (1030, 333)])
+def test_fp64_equality_hessian_mode_parity(ctx, alg, n, p):
+    """K = {0}, rho > 0: the grid engine precomputes H = Q + rho G'G and runs one product
+    per inner iteration; at equal counts it follows the oracle's two-matrix form to 1e-9."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.equality_dense(n=n, p=p, seed=11 + n, lam_lo=1.0, lam_hi=30.0)
+    c = _eq_constants(inst, alg)
+    ro = O.dfom(_eq_qp(inst), ALG_IDS[alg], c, inner_fixed=6, outer_fixed=4)
+    P = gpu_problem(ctx, inst, D.FP64, cone=D.CONE_EQ)
+    xl, xa, lam, (r,) = P.solve(gpu_opts_from(c, alg, fixed_inner=6, fixed_outer=4, engine=D.ENGINE_GRID))
+    assert r.inner_iters == ro.inner_iters
+    assert rel(xl, ro.x_last) <= 1e-9 and rel(xa, ro.x_avg) <= 1e-9
+    assert rel(lam, ro.lam) <= 1e-9
+
+
+def test_fp32_equality_hessian_matches_two_matrix_form(ctx, monkeypatch):
+    """The Hessian mode and the two-matrix augmented form give the same FP32 iterates up to
+    rounding, on a size with ragged row tiles; both stay within FP32 accuracy of the oracle."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.equality_dense(n=1028, p=301, seed=5, lam_lo=1.0, lam_hi=30.0)
+    c = _eq_constants(inst, "ADFGM")
+    o = gpu_opts_from(c, "ADFGM", fixed_inner=8, fixed_outer=3, engine=D.ENGINE_GRID)
+    P = gpu_problem(ctx, inst, D.FP32, cone=D.CONE_EQ)
+    monkeypatch.setenv("DQ_GRID_HESSIAN", "0")
+    x1, a1, l1, _ = P.solve(o)
+    monkeypatch.setenv("DQ_GRID_HESSIAN", "1")
+    x2, a2, l2, _ = P.solve(o)
+    ro = O.dfom(_eq_qp(inst), O.ADFGM, c, inner_fixed=8, outer_fixed=3)
+    assert rel(x2, x1) <= 1e-4 and rel(l2, l1) <= 1e-3
+    assert rel(x2, ro.x_last) <= 1e-4 and rel(x1, ro.x_last) <= 1e-4
+
+
+@pytest.mark.parametrize("n,p,n_zero", [(300, 80, 0), (200, 50, 30)])
+def test_fp32_equality_eps_optimal(ctx, n, p, n_zero):
+    """K = {0}, Q >= 0 (singular when n_zero > 0, the paper's equality-constrained case):
+    the FP32 certified output is eps-optimal when re-scored in FP64 by the oracle (its d_lb is
+    a lower bound of F* whether or not its own run converged)."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.equality_dense(n=n, p=p, seed=9 + n_zero, lam_lo=1.0, lam_hi=20.0, n_zero=n_zero)
+    qp = _eq_qp(inst)
+    eps = 1e-3
+    c = O.constants(qp, O.ADFGM, lmin_Q=inst.lmin_Q)
+    ref = O.dfom(qp, O.ADFGM, c, eps_out=1e-5, eps_in=1e-6, outer_check_every=5, max_outer=3000)
+    P = gpu_problem(ctx, inst, D.FP32, cone=D.CONE_EQ)
+    xl, xa, lam, (r,) = P.solve(D.opts("ADFGM", eps_out=eps, eps_in=1e-5, max_outer=20000, check_every=5,
+                                       engine=D.ENGINE_GRID))
+    assert r.status == 0
+    x = xl if r.converged_last else xa
+    assert O.infeas(qp, x) <= eps * 1.01
+    assert O.F(qp, x) - ref.d_lb <= eps * 1.01

@@ -232,3 +232,26 @@ def uneven_batch_device(count=10000, seed=3, n_lo=16, n_hi=512, device="cuda", d
                           g=g[k].to(dtype).contiguous(), lb=-torch.ones(n, device=device, dtype=dtype),
                           ub=torch.ones(n, device=device, dtype=dtype))
     return out
+
+
+def equality_dense(n=300, p=100, seed=0, lam_lo=1.0, lam_hi=100.0, n_zero=0, box=1.0) -> Instance:
+    """Dense QP with equality constraints (K = {0}), feasible by construction.
+
+    Q = U diag(lam) U' with lam ~ U[lam_lo, lam_hi] and n_zero of them set to 0
+    (Q singular, the paper's Q >= 0 case); G ~ N(0, 1/n); g = -G u0 with
+    u0 ~ U[-box/2, box/2] inside the box [-box, box]; q ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    U = haar(rng, n)
+    lam = rng.uniform(lam_lo, lam_hi, n)
+    lam[:n_zero] = 0.0
+    Q = (U * lam[None, :]) @ U.T
+    Q = 0.5 * (Q + Q.T)
+    q = rng.standard_normal(n)
+    G = rng.standard_normal((p, n)) / np.sqrt(n)
+    u0 = rng.uniform(-0.5 * box, 0.5 * box, n)
+    g = -G @ u0
+    lb = -box * np.ones(n)
+    ub = box * np.ones(n)
+    inst = Instance(Q, q, G, g, lb, ub, float(lam.min()), float(lam.max()), "ADFGM",
+                    {"kind": "equality_dense", "seed": seed, "cone": 1})
+    return inst
