@@ -48,50 +48,69 @@ struct CtaInst {
 };
 
 // out[i] = sum_j M[j*ld + i] v[j], i < cols, j < rows  (out = M' v).
-// The rows are split into S contiguous segments (S depends on cols only: 8
-// for cols <= 32 down to 1 for cols > 128, so that narrow products still
-// occupy the block); a (segment, column) pair runs 8 independent accumulators
-// (8 loads in flight when M is in global memory), and the S partial sums are
-// added in segment order in `part` (S * cols <= 256 elements).  The order of
-// every sum is fixed by (rows, cols) alone: results do not depend on the block
-// size or on whether M sits in shared or global memory.
+// Work units of one lane: cpw columns 32 apart (cpw = 4 for cols >= 128, 2 for
+// cols >= 64, else 1; a warp's load covers 128 contiguous bytes) over one of S
+// contiguous row segments, S chosen for about 512 units.  A unit walks its rows
+// four at a time (16 loads in flight for cpw = 4), even rows into one
+// accumulator and odd rows into another, and the S segment sums are added in
+// segment order in `part` (at most 2048 elements).  Every sum's order is fixed
+// by (rows, cols) alone: results do not depend on the block size or on whether
+// M sits in shared or global memory.
 template <typename A, typename T, typename V>
 __device__ __forceinline__ void mtv(const T* __restrict__ M, int rows, int cols, int ld,
                                     const V* __restrict__ v, A* __restrict__ out, A* __restrict__ part) {
-  const int cp = (cols + 31) & ~31;
-  const int S = cp >= 256 ? 1 : min(8, 256 / cp);
-  for (int q = threadIdx.x; q < S * cp; q += blockDim.x) {
-    const int sg = q / cp, c = q - sg * cp;
-    if (c >= cols) continue;
+  const int cpw = cols >= 128 ? 4 : (cols >= 64 ? 2 : 1);
+  const int bw = 32 * cpw, units = ((cols + bw - 1) / bw) * 32;
+  const int S = units >= 512 ? 1 : min(8, 512 / units);
+  for (int q = threadIdx.x; q < S * units; q += blockDim.x) {
+    const int sg = q / units, rem = q - sg * units;
+    const int cbase = (rem >> 5) * bw + (rem & 31);
     const int r0 = (int)((long long)rows * sg / S), r1 = (int)((long long)rows * (sg + 1) / S);
-    const T* col = M + c;
-    A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0), a4 = A(0), a5 = A(0), a6 = A(0), a7 = A(0);
+    A e[4], o[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) e[u] = o[u] = A(0);
+    bool cv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cv[u] = u < cpw && cbase + 32 * u < cols;
     int j = r0;
-    for (; j + 8 <= r1; j += 8) {
-      const T m0 = col[(size_t)(j + 0) * ld], m1 = col[(size_t)(j + 1) * ld];
-      const T m2 = col[(size_t)(j + 2) * ld], m3 = col[(size_t)(j + 3) * ld];
-      const T m4 = col[(size_t)(j + 4) * ld], m5 = col[(size_t)(j + 5) * ld];
-      const T m6 = col[(size_t)(j + 6) * ld], m7 = col[(size_t)(j + 7) * ld];
-      a0 += A(m0) * A(v[j + 0]);
-      a1 += A(m1) * A(v[j + 1]);
-      a2 += A(m2) * A(v[j + 2]);
-      a3 += A(m3) * A(v[j + 3]);
-      a4 += A(m4) * A(v[j + 4]);
-      a5 += A(m5) * A(v[j + 5]);
-      a6 += A(m6) * A(v[j + 6]);
-      a7 += A(m7) * A(v[j + 7]);
+    for (; j + 4 <= r1; j += 4) {
+      T m[4][4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m[r][u] = cv[u] ? M[(size_t)(j + r) * ld + cbase + 32 * u] : T(0);
+      const A v0 = A(v[j]), v1 = A(v[j + 1]), v2 = A(v[j + 2]), v3 = A(v[j + 3]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        e[u] += A(m[0][u]) * v0;
+        o[u] += A(m[1][u]) * v1;
+        e[u] += A(m[2][u]) * v2;
+        o[u] += A(m[3][u]) * v3;
+      }
     }
-    for (; j < r1; ++j) a0 += A(col[(size_t)j * ld]) * A(v[j]);
-    const A r = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
-    if (S == 1) out[c] = r;
-    else part[sg * cols + c] = r;
+    for (; j < r1; ++j) {
+      const A vj = A(v[j]);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const A mv = cv[u] ? A(M[(size_t)j * ld + cbase + 32 * u]) : A(0);
+        if ((j - r0) & 1) o[u] += mv * vj;
+        else e[u] += mv * vj;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (!cv[u]) continue;
+      const int c = cbase + 32 * u;
+      if (S == 1) out[c] = e[u] + o[u];
+      else part[sg * cols + c] = e[u] + o[u];
+    }
   }
   if (S > 1) {
     __syncthreads();
     for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-      A o = part[c];
-      for (int sg = 1; sg < S; ++sg) o += part[sg * cols + c];
-      out[c] = o;
+      A r = part[c];
+      for (int sg = 1; sg < S; ++sg) r += part[sg * cols + c];
+      out[c] = r;
     }
   }
 }
@@ -121,7 +140,7 @@ struct CtaWs {
   XState<T> A, B;        // main warm-start chain, extra last-iterate solve
   T *c, *tn, *w, *mu, *lam, *lamp, *ul, *uavg;
   double *usum, *dn, *dp, *red;
-  T* part;               // 256 partial sums of the segmented products
+  T* part;               // 2048 partial sums of the segmented products
   const T *Q, *G, *GT;
 };
 
@@ -486,7 +505,7 @@ __host__ __device__ inline size_t cta_vec_bytes(int n, int p) {
   b += 2 * (6 * a16(n * sizeof(T)) + 3 * a16(pn * sizeof(T)));  // A, B states
   b += 4 * a16(n * sizeof(T));                                   // c, tn, ul, uavg
   b += 4 * a16(pn * sizeof(T));                                  // w, mu, lam, lamp
-  b += a16(256 * sizeof(T));                                     // part
+  b += a16(2048 * sizeof(T));                                    // part
   return b;
 }
 template <typename T>
@@ -524,7 +543,7 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
   W.mu = (T*)take(pn * sizeof(T));
   W.lam = (T*)take(pn * sizeof(T));
   W.lamp = (T*)take(pn * sizeof(T));
-  W.part = (T*)take(256 * sizeof(T));
+  W.part = (T*)take(2048 * sizeof(T));
   W.Q = I.Q; W.G = I.G; W.GT = I.GT;
   // stage the matrices in shared memory when they fit
   const size_t nn = (size_t)n * n, np_ = (size_t)n * p;
