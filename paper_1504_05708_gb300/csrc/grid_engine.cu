@@ -722,6 +722,7 @@ struct GridRun {
   }
 
   // ---- single-pass iteration (grid_v2.cuh): setup and launch
+  static constexpr double kV2GWeight = 1.0;
   bool use_v2 = false;
   int v2_nQ = 0, v2_nG = 0, v2_npt = 0;
   size_t v2_smem = 0;
@@ -760,7 +761,12 @@ struct GridRun {
       W->v2_src = (const void*)Qm();
     }
     // CTA roles in proportion to the bytes each matrix contributes
-    const double bq = double(W->hoff[n]), bg = aug ? double(p) * n : 0.0;
+    // CTA roles in proportion to the cost of each matrix: a G row costs two passes over
+    // shared memory (dot, then the update once w_j is known) and a barrier, so its bytes
+    // weigh g_weight times a packed Q row's (DQ_V2_GWEIGHT overrides the default)
+    const char* gw_env = getenv("DQ_V2_GWEIGHT");
+    const double g_weight = gw_env ? atof(gw_env) : kV2GWeight;
+    const double bq = double(W->hoff[n]), bg = aug ? g_weight * double(p) * n : 0.0;
     int nQ = aug && p > 0 ? (int)lround(B2 * bq / (bq + bg)) : B2;
     nQ = std::max(1, std::min(nQ, aug && p > 0 ? B2 - 1 : B2));
     const int nG = aug && p > 0 ? B2 - nQ : 0;

@@ -4,7 +4,7 @@
 // a different initial state per instance) turn the matrix-vector products of
 // Algorithm FOM (Sec. 2.1) and of the dual step of Algorithm DFOM (Sec. 3)
 // into matrix-matrix products over the batch.  One persistent thread block
-// (128 threads) takes a tile of 128 instances and runs its whole solve --
+// (256 threads, two per instance) takes a tile of 128 instances and runs its whole solve --
 // every outer iteration, the inner loops, the outer stopping checks and the
 // extra last-iterate solves -- without returning to the host:
 //   * TMEM lane b holds instance b: four 16-aligned column regions hold
@@ -101,18 +101,24 @@ __device__ __forceinline__ void kahan(float& s, float& c, float v) {
   s = t;
 }
 
-// Per-block state of the pipeline (uniform across the block's threads).
+// Per-block state of the pipeline (uniform across the block's threads).  The
+// block has 256 threads: thread (half h, lane l) works on TMEM lane l, columns
+// 8h..8h+7 of every 16-column group (warps 4..7 reach the same TMEM lane
+// quadrants as warps 0..3), so each lane's epilogue is split over two threads.
+static constexpr int TC_THREADS = 2 * TM;
+
 struct TcCtx {
   const TcArgs* a;
   uint8_t *Qh, *Ql, *Ah, *Al;
   uint8_t* B0;                  // chunk buffers: buffer b hi at B0 + 2 b bb, lo at B0 + (2 b + 1) bb
   size_t ab, bb;                // bytes of one operand half (hi or lo); of one chunk half
   float *lb, *ub;
+  float* red;                   // [4][2][TM] per-lane partial sums of the two halves
   uint64_t *bar_mma, *bar_tx;   // [2] each
   uint32_t ph_mma, ph_tx;       // phase bit of barrier b at bit b
   uint32_t tm, lane_off;
   uint32_t rD, rY, rX, rC;       // TMEM column regions
-  int tid, NPAD;
+  int tid, lane, half, NPAD;
   bool ok;
 
   __device__ void sync_async() {  // operand writes visible to the tensor core, TMEM ops ordered
@@ -121,6 +127,13 @@ struct TcCtx {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
+  }
+  // The two halves' partial sums of up to four per-lane values, added in half order.
+  __device__ void combine(float (&v)[4], int cnt) {
+    for (int i = 0; i < cnt; ++i) red[(i * 2 + half) * TM + lane] = v[i];
+    __syncthreads();
+    for (int i = 0; i < cnt; ++i) v[i] = red[(i * 2) * TM + lane] + red[(i * 2 + 1) * TM + lane];
+    __syncthreads();
   }
   __device__ __forceinline__ uint8_t* Bh(int b) const { return B0 + (size_t)(2 * b) * bb; }
   __device__ __forceinline__ uint8_t* Bl(int b) const { return B0 + (size_t)(2 * b + 1) * bb; }
@@ -146,26 +159,32 @@ struct TcCtx {
     }
     wait_mma(0);
   }
+  // this thread's 8 columns of group c0 of region r
+  __device__ __forceinline__ void ld8(uint32_t r, int c0, uint32_t (&v)[8]) const {
+    tc::tmem_ld8(tm + lane_off + r + c0 + 8 * half, v);
+  }
+  __device__ __forceinline__ void st8(uint32_t r, int c0, const uint32_t (&v)[8]) const {
+    tc::tmem_st8(tm + lane_off + r + c0 + 8 * half, v);
+  }
   // operand <- TMEM region r
   __device__ void operand_from(uint32_t r) {
     for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      uint32_t v[16];
-      tc::tmem_ld16(tm + lane_off + r + c0, v);
+      uint32_t v[8];
+      ld8(r, c0, v);
       tc::tmem_ld_wait();
-      float f[16];
+      float f[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) f[i] = __uint_as_float(v[i]);
-      put8(Ah, Al, tid, c0, f);
-      put8(Ah, Al, tid, c0 + 8, f + 8);
+      for (int i = 0; i < 8; ++i) f[i] = __uint_as_float(v[i]);
+      put8(Ah, Al, lane, c0 + 8 * half, f);
     }
   }
   // region dst <- region src
   __device__ void region_copy(uint32_t dst, uint32_t src) {
     for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      uint32_t v[16];
-      tc::tmem_ld16(tm + lane_off + src + c0, v);
+      uint32_t v[8];
+      ld8(src, c0, v);
       tc::tmem_ld_wait();
-      tc::tmem_st16(tm + lane_off + dst + c0, v);
+      st8(dst, c0, v);
     }
   }
 
@@ -178,7 +197,7 @@ struct TcCtx {
     const int nch = A.nchG;
     if (nch == 0) return;
     const uint32_t cb = (uint32_t)A.NC * NPAD * 2;  // bytes of one packed chunk (hi or lo)
-    const uint32_t sdelta = rY - rD;  // accumulator slot b at rD + b * sdelta
+    const uint32_t sdelta = rY - rD;                // accumulator slot b at rD + b * sdelta
     if (tid == 0) {
       issue_B(0, A.Ghi, A.Glo, cb);
       if (nch > 1) issue_B(1, A.Ghi + cb / 16, A.Glo + cb / 16, cb);
@@ -217,16 +236,18 @@ struct TcCtx {
     const size_t abytes = (size_t)TM * TC_KC * 2;  // chunk b: hi at Ah + 2 b abytes, lo next
     auto AH = [&](int b) { return Ah + (size_t)(2 * b) * abytes; };
     auto AL = [&](int b) { return Ah + (size_t)(2 * b + 1) * abytes; };
-    auto build = [&](int ch, int b) {  // all KC loads in flight before the shared-memory stores
+    auto build = [&](int ch, int b) {  // this half's 3 groups of 8: every load in flight before the stores
       const int j0 = ch * TC_KC;
-      float v[TC_KC];
+      float v[TC_KC / 2];
 #pragma unroll
-      for (int i = 0; i < TC_KC; ++i) {
-        const int j = j0 + i;
-        v[i] = j < p ? __ldcg(m + im(tile, p, j, tid)) : 0.f;
-      }
+      for (int g = 0; g < TC_KC / 16; ++g)
 #pragma unroll
-      for (int k0 = 0; k0 < TC_KC; k0 += 8) put8(AH(b), AL(b), tid, k0, v + k0);
+        for (int i = 0; i < 8; ++i) {
+          const int j = j0 + 16 * g + 8 * half + i;
+          v[8 * g + i] = j < p ? __ldcg(m + im(tile, p, j, lane)) : 0.f;
+        }
+#pragma unroll
+      for (int g = 0; g < TC_KC / 16; ++g) put8(AH(b), AL(b), lane, 16 * g + 8 * half, v + 8 * g);
     };
     if (nch > 0) {
       build(0, 0);
@@ -253,21 +274,21 @@ struct TcCtx {
     }
     // c = acc + q
     for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      uint32_t v[16];
+      uint32_t v[8];
       if (nch > 0) {
-        tc::tmem_ld16(tm + lane_off + rC + c0, v);
+        ld8(rC, c0, v);
         tc::tmem_ld_wait();
       } else {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0u;
+        for (int i = 0; i < 8; ++i) v[i] = 0u;
       }
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = c0 + i;
-        const float qv = col < A.n ? A.qT[im(tile, A.n, col, tid)] : 0.f;
+      for (int i = 0; i < 8; ++i) {
+        const int col = c0 + 8 * half + i;
+        const float qv = col < A.n ? A.qT[im(tile, A.n, col, lane)] : 0.f;
         v[i] = __float_as_uint(__uint_as_float(v[i]) + qv);
       }
-      tc::tmem_st16(tm + lane_off + rC + c0, v);
+      st8(rC, c0, v);
     }
     sync_async();
   }
@@ -279,7 +300,7 @@ struct TcCtx {
 // certificate and iteration count.  Lanes with active == false keep x.
 __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out, int& kin_out) {
   const TcArgs& A = *C.a;
-  const int NPAD = C.NPAD, tid = C.tid;
+  const int NPAD = C.NPAD, h8 = 8 * C.half;
   const float L = A.L;
   // y^0 = x^0; D = Q x^0
   C.region_copy(C.rY, C.rX);
@@ -307,19 +328,19 @@ __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out,
     }
     // x^k = [y - (Q y + c)/L]_U,  y^k = x^k + beta (x^k - x^{k-1})
     for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      uint32_t d[16], y[16], x[16], c[16];
-      tc::tmem_ld16(C.tm + C.lane_off + C.rD + c0, d);
-      tc::tmem_ld16(C.tm + C.lane_off + C.rY + c0, y);
-      tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
-      tc::tmem_ld16(C.tm + C.lane_off + C.rC + c0, c);
+      uint32_t d[8], y[8], x[8], c[8];
+      C.ld8(C.rD, c0, d);
+      C.ld8(C.rY, c0, y);
+      C.ld8(C.rX, c0, x);
+      C.ld8(C.rC, c0, c);
       tc::tmem_ld_wait();
-      uint32_t xn[16], yn[16];
-      float op[16];
+      uint32_t xn[8], yn[8];
+      float op[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < 8; ++i) {
         const float yv = __uint_as_float(y[i]), xv = __uint_as_float(x[i]);
         const float s = yv - (__uint_as_float(d[i]) + __uint_as_float(c[i])) / L;
-        const float lo = C.lb[c0 + i], hi = C.ub[c0 + i];
+        const float lo = C.lb[c0 + h8 + i], hi = C.ub[c0 + h8 + i];
         float xnew = s < lo ? lo : (s > hi ? hi : s);
         float ynew = xnew + beta * (xnew - xv);
         if (done) {
@@ -330,29 +351,29 @@ __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out,
         yn[i] = __float_as_uint(ynew);
         op[i] = check ? xnew : ynew;
       }
-      tc::tmem_st16(C.tm + C.lane_off + C.rX + c0, xn);
-      tc::tmem_st16(C.tm + C.lane_off + C.rY + c0, yn);
-      put8(C.Ah, C.Al, tid, c0, op);
-      put8(C.Ah, C.Al, tid, c0 + 8, op + 8);
+      C.st8(C.rX, c0, xn);
+      C.st8(C.rY, c0, yn);
+      put8(C.Ah, C.Al, C.lane, c0 + h8, op);
     }
     C.sync_async();
     C.mma_Q();
     if (__syncthreads_or(!C.ok)) break;  // a bounded wait gave up: leave with the error flag set
     if (!check) continue;
     // D = Q x^k: certificate of eq. duquad_in (gradient-mapping bound, or the
-    // Frank-Wolfe gap when sigma = 0), compensated FP32 sum
+    // Frank-Wolfe gap when sigma = 0), compensated FP32 sums of the two halves
     float cs = 0.f, cc = 0.f;
     for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      uint32_t d[16], x[16], c[16];
-      tc::tmem_ld16(C.tm + C.lane_off + C.rD + c0, d);
-      tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
-      tc::tmem_ld16(C.tm + C.lane_off + C.rC + c0, c);
+      uint32_t d[8], x[8], c[8];
+      C.ld8(C.rD, c0, d);
+      C.ld8(C.rX, c0, x);
+      C.ld8(C.rC, c0, c);
       tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        if (c0 + i >= A.n) continue;
+      for (int i = 0; i < 8; ++i) {
+        const int col = c0 + h8 + i;
+        if (col >= A.n) continue;
         const float gd = __uint_as_float(d[i]) + __uint_as_float(c[i]), xv = __uint_as_float(x[i]);
-        const float lo = C.lb[c0 + i], hi = C.ub[c0 + i];
+        const float lo = C.lb[col], hi = C.ub[col];
         if (fgm_sigma) {
           const float xp = fminf(fmaxf(xv - gd / L, lo), hi);
           const float dd = xv - xp;
@@ -363,7 +384,9 @@ __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out,
         }
       }
     }
-    const float cv = cs - cc;
+    float tot[4] = {cs - cc, 0.f, 0.f, 0.f};
+    C.combine(tot, 1);
+    const float cv = tot[0];
     const bool stop = A.inner_fixed > 0 || cv <= A.eps_in || k >= kmax;
     if (stop && !done) {
       done = true;
@@ -373,19 +396,18 @@ __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out,
     if (__syncthreads_and(done)) break;
     // continue: frozen lanes present x (y = x), the others y^k
     for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      uint32_t y[16], x[16];
-      tc::tmem_ld16(C.tm + C.lane_off + C.rY + c0, y);
-      tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+      uint32_t y[8], x[8];
+      C.ld8(C.rY, c0, y);
+      C.ld8(C.rX, c0, x);
       tc::tmem_ld_wait();
-      float op[16];
+      float op[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < 8; ++i) {
         if (done) y[i] = x[i];
         op[i] = __uint_as_float(y[i]);
       }
-      tc::tmem_st16(C.tm + C.lane_off + C.rY + c0, y);
-      put8(C.Ah, C.Al, tid, c0, op);
-      put8(C.Ah, C.Al, tid, c0 + 8, op + 8);
+      C.st8(C.rY, c0, y);
+      put8(C.Ah, C.Al, C.lane, c0 + h8, op);
     }
     C.sync_async();
     C.mma_Q();
@@ -396,50 +418,54 @@ __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out,
 
 // F(x) = x'Qx/2 + q'x of the lane's x (TMEM region rx), FP32 from the FP32 Q:
 // Q is staged in the bulk-copy buffers and every lane's x in the operand area
-// (instance-minor, conflict-free), both free at this point.  Row sums use
-// four accumulators over the upper triangle, rows are added with Kahan.
+// (instance-minor, conflict-free), both free at this point.  Rows alternate
+// between the two halves; row sums use four accumulators over the upper
+// triangle, rows are added with Kahan, and the halves are combined in order.
 __device__ __forceinline__ float tc_F(TcCtx& C, int tile, uint32_t rx) {
   const TcArgs& A = *C.a;
-  const int n = A.n, tid = C.tid;
+  const int n = A.n, lane = C.lane;
   float* Xs = (float*)C.Ah;
   float* Qs = (float*)C.B0;
   {  // Q into shared memory, eight loads in flight per thread before the stores
     const int nn = n * n;
-    for (int e0 = tid; e0 < nn; e0 += 8 * TM) {
+    for (int e0 = C.tid; e0 < nn; e0 += 8 * TC_THREADS) {
       float t8[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) t8[u] = e0 + u * TM < nn ? __ldg(A.Qf + e0 + u * TM) : 0.f;
+      for (int u = 0; u < 8; ++u) t8[u] = e0 + u * TC_THREADS < nn ? __ldg(A.Qf + e0 + u * TC_THREADS) : 0.f;
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (e0 + u * TM < nn) Qs[e0 + u * TM] = t8[u];
+        if (e0 + u * TC_THREADS < nn) Qs[e0 + u * TC_THREADS] = t8[u];
     }
   }
   for (int c0 = 0; c0 < C.NPAD; c0 += 16) {
-    uint32_t x[16];
-    tc::tmem_ld16(C.tm + C.lane_off + rx + c0, x);
+    uint32_t x[8];
+    C.ld8(rx, c0, x);
     tc::tmem_ld_wait();
 #pragma unroll
-    for (int i = 0; i < 16; ++i)
-      if (c0 + i < n) Xs[(c0 + i) * TM + tid] = __uint_as_float(x[i]);
+    for (int i = 0; i < 8; ++i) {
+      const int col = c0 + 8 * C.half + i;
+      if (col < n) Xs[col * TM + lane] = __uint_as_float(x[i]);
+    }
   }
   __syncthreads();
   float s = 0.f, c = 0.f;
-  for (int i = 0; i < n; ++i) {
+  for (int i = C.half; i < n; i += 2) {
     const float* Qr = Qs + (size_t)i * n;
-    const float xi = Xs[i * TM + tid];
+    const float xi = Xs[i * TM + lane];
     float a0 = 0.5f * Qr[i] * xi, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     int k = i + 1;
     for (; k + 4 <= n; k += 4) {
-      a0 = fmaf(Qr[k], Xs[k * TM + tid], a0);
-      a1 = fmaf(Qr[k + 1], Xs[(k + 1) * TM + tid], a1);
-      a2 = fmaf(Qr[k + 2], Xs[(k + 2) * TM + tid], a2);
-      a3 = fmaf(Qr[k + 3], Xs[(k + 3) * TM + tid], a3);
+      a0 = fmaf(Qr[k], Xs[k * TM + lane], a0);
+      a1 = fmaf(Qr[k + 1], Xs[(k + 1) * TM + lane], a1);
+      a2 = fmaf(Qr[k + 2], Xs[(k + 2) * TM + lane], a2);
+      a3 = fmaf(Qr[k + 3], Xs[(k + 3) * TM + lane], a3);
     }
-    for (; k < n; ++k) a0 = fmaf(Qr[k], Xs[k * TM + tid], a0);
-    kahan(s, c, xi * (((a0 + a1) + (a2 + a3)) + A.qT[im(tile, n, i, tid)]));
+    for (; k < n; ++k) a0 = fmaf(Qr[k], Xs[k * TM + lane], a0);
+    kahan(s, c, xi * (((a0 + a1) + (a2 + a3)) + A.qT[im(tile, n, i, lane)]));
   }
-  __syncthreads();  // the buffers are reused by the next product
-  return s - c;
+  float v[4] = {s - c, 0.f, 0.f, 0.f};
+  C.combine(v, 1);  // also orders the shared-memory reads before the buffers' next use
+  return v[0];
 }
 
 // dist_K(Gx + g)^2 and sum_j m_j (Gx + g)_j for the operand x (m nullable);
@@ -447,36 +473,39 @@ __device__ __forceinline__ float tc_F(TcCtx& C, int tile, uint32_t rx) {
 __device__ __forceinline__ void tc_resid(TcCtx& C, int tile, const float* m, float& inf2, float& lag, int& neg) {
   const TcArgs& A = *C.a;
   float is = 0.f, ic = 0.f, ls = 0.f, lc = 0.f;
-  int ng = 0;
+  float ng = 0.f;
   C.g_product([&](int ch, uint32_t slot) {
     const int j0 = ch * A.NC;
     for (int c0 = 0; c0 < A.NC; c0 += 16) {
-      uint32_t r[16];
-      tc::tmem_ld16(C.tm + C.lane_off + slot + c0, r);
+      uint32_t r[8];
+      C.ld8(slot, c0, r);
       tc::tmem_ld_wait();
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int j = j0 + c0 + i;
+      for (int i = 0; i < 8; ++i) {
+        const int j = j0 + c0 + 8 * C.half + i;
         if (j >= A.p) continue;
-        const float rv = __uint_as_float(r[i]) + A.gT[im(tile, A.p, j, C.tid)];
+        const float rv = __uint_as_float(r[i]) + A.gT[im(tile, A.p, j, C.lane)];
         const float dk = rv - proj_K(A.cone, rv);
         kahan(is, ic, dk * dk);
         if (m) {
-          const float mj = m[im(tile, A.p, j, C.tid)];
-          ng |= mj < 0.f;
+          const float mj = m[im(tile, A.p, j, C.lane)];
+          if (mj < 0.f) ng = 1.f;
           kahan(ls, lc, mj * rv);
         }
       }
     }
   });
-  inf2 = is - ic;
-  lag = ls - lc;
-  neg = ng;
+  float v[4] = {is - ic, ls - lc, ng, 0.f};
+  C.combine(v, 3);
+  inf2 = v[0];
+  lag = v[1];
+  neg = v[2] > 0.f;
 }
 
-__global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ __align__(8) uint64_t bar_mma[2], bar_tx[2], bar_q;
+  __shared__ float s_red[4 * 2 * TM];
   __shared__ uint32_t s_taddr;
   __shared__ int s_tile;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -484,8 +513,12 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
   TcCtx C;
   C.a = &a;
   C.tid = tid;
+  C.lane = tid & (TM - 1);
+  C.half = tid / TM;
   C.NPAD = NPAD;
   C.ok = true;
+  C.red = s_red;
+  const int lane = C.lane, half = C.half, h8 = 8 * half;
   size_t off = 0;
   auto take = [&](size_t b) {
     uint8_t* r = sm + off;
@@ -506,7 +539,7 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
   C.B0 = take(4 * C.bb);
   C.lb = (float*)take((size_t)NPAD * 4);
   C.ub = (float*)take((size_t)NPAD * 4);
-  for (int i = tid; i < NPAD; i += TM) {
+  for (int i = tid; i < NPAD; i += TC_THREADS) {
     C.lb[i] = i < n ? a.lb[i] : 0.f;
     C.ub[i] = i < n ? a.ub[i] : 0.f;
   }
@@ -537,7 +570,7 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
   tc::fence_after();
   C.ok = tc::mbar_wait(&bar_q, 0, kTcWaitNs);
   C.tm = s_taddr;
-  C.lane_off = (uint32_t)(warp * 32) << 16;
+  C.lane_off = (uint32_t)((warp & 3) * 32) << 16;
   C.rD = 0;
   C.rY = NPAD;
   C.rX = 2 * NPAD;
@@ -549,35 +582,35 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
     const int tile = s_tile;
     __syncthreads();
     if (tile >= a.ntiles || !C.ok) break;
-    const int b = tile * TM + tid;
+    const int b = tile * TM + lane;
     const bool valid = b < a.B;
     // ---- x^0 = warm start or [0]_U; lambda^0 = mu^1 = warm start or 0
     for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      uint32_t v[16];
+      uint32_t v[8];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int col = c0 + i;
+      for (int i = 0; i < 8; ++i) {
+        const int col = c0 + h8 + i;
         float x = 0.f;
-        if (col < n) x = (valid && a.x0T) ? a.x0T[im(tile, n, col, tid)] : fminf(fmaxf(0.f, C.lb[col]), C.ub[col]);
+        if (col < n) x = (valid && a.x0T) ? a.x0T[im(tile, n, col, lane)] : fminf(fmaxf(0.f, C.lb[col]), C.ub[col]);
         v[i] = __float_as_uint(x);
       }
-      tc::tmem_st16(C.tm + C.lane_off + C.rX + c0, v);
+      C.st8(C.rX, c0, v);
     }
-    for (int j0 = 0; j0 < p; j0 += 16) {
+    for (int j0 = 16 * half; j0 < p; j0 += 32) {
       float l0[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i)
-        l0[i] = (valid && a.lam0T && j0 + i < p) ? __ldg(a.lam0T + im(tile, p, j0 + i, tid)) : 0.f;
+        l0[i] = (valid && a.lam0T && j0 + i < p) ? __ldg(a.lam0T + im(tile, p, j0 + i, lane)) : 0.f;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         if (j0 + i >= p) continue;
-        const size_t ix = im(tile, p, j0 + i, tid);
+        const size_t ix = im(tile, p, j0 + i, lane);
         a.lam[ix] = l0[i];
         a.lamp[ix] = l0[i];
         a.mu[ix] = l0[i];
       }
     }
-    for (int i = 0; i < n; ++i) a.usum[im(tile, n, i, tid)] = 0.f;
+    for (int i = half; i < n; i += 2) a.usum[im(tile, n, i, lane)] = 0.f;
     C.sync_async();
     C.gt_product(tile, a.mu);  // c = q + G' mu^1
 
@@ -601,35 +634,34 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
         th_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
         beta = (theta - 1.0) / th_next;
       }
-      float is = 0.f, ic = 0.f, ls = 0.f, lc = 0.f;
-      int mu_neg = 0;
+      float is = 0.f, ic = 0.f, ls = 0.f, lc = 0.f, mneg = 0.f;
       C.g_product([&](int ch, uint32_t slot) {
         const int j0 = ch * a.NC;
         for (int c0 = 0; c0 < a.NC; c0 += 16) {
-          uint32_t r[16];
-          tc::tmem_ld16(C.tm + C.lane_off + slot + c0, r);
+          uint32_t r[8];
+          C.ld8(slot, c0, r);
           tc::tmem_ld_wait();
           if (!act) continue;
-          // every load of the 16 columns is issued before the first store
-          float gv[16], mv[16], lv[16];
+          // every load of this thread's 8 columns is issued before the first store
+          float gv[8], mv[8], lv[8];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int j = j0 + c0 + i;
-            const size_t ix = im(tile, p, j < p ? j : 0, tid);
+          for (int i = 0; i < 8; ++i) {
+            const int j = j0 + c0 + h8 + i;
+            const size_t ix = im(tile, p, j < p ? j : 0, lane);
             gv[i] = __ldcg(a.gT + ix);
             mv[i] = __ldcg(a.mu + ix);
             lv[i] = __ldcg(a.lam + ix);
           }
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int j = j0 + c0 + i;
+          for (int i = 0; i < 8; ++i) {
+            const int j = j0 + c0 + h8 + i;
             if (j >= p) continue;
-            const size_t ix = im(tile, p, j, tid);
+            const size_t ix = im(tile, p, j, lane);
             const float rv = __uint_as_float(r[i]) + gv[i];
             const float muj = mv[i], lold = lv[i];
             if (eval) {
               kahan(ls, lc, muj * rv);
-              mu_neg |= muj < 0.f;
+              if (muj < 0.f) mneg = 1.f;
               const float dk = rv - proj_K(a.cone, rv);
               kahan(is, ic, dk * dk);
             }
@@ -642,16 +674,16 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
       });
       // averaging weight theta_k (eq. average_primal)
       for (int c0 = 0; c0 < NPAD; c0 += 16) {
-        uint32_t x[16];
-        tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+        uint32_t x[8];
+        C.ld8(C.rX, c0, x);
         tc::tmem_ld_wait();
         if (!act) continue;
-        float us[16];
+        float us[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) us[i] = c0 + i < n ? __ldcg(a.usum + im(tile, n, c0 + i, tid)) : 0.f;
+        for (int i = 0; i < 8; ++i) us[i] = c0 + h8 + i < n ? __ldcg(a.usum + im(tile, n, c0 + h8 + i, lane)) : 0.f;
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (c0 + i < n) a.usum[im(tile, n, c0 + i, tid)] = us[i] + (float)theta * __uint_as_float(x[i]);
+        for (int i = 0; i < 8; ++i)
+          if (c0 + h8 + i < n) a.usum[im(tile, n, c0 + h8 + i, lane)] = us[i] + (float)theta * __uint_as_float(x[i]);
       }
       if (act) {
         S += theta;
@@ -659,18 +691,20 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
         kout = k;
       }
       if (eval) {
+        float ev[4] = {ls - lc, is - ic, mneg, 0.f};
+        C.combine(ev, 3);
         // lower bound from (ubar^k, mu^k) when mu^k is a valid multiplier
         const float Fu = tc_F(C, tile, C.rX);
-        if (act && (a.cone == CONE_EQ || !mu_neg)) d_lb = fmaxf(d_lb, Fu + (ls - lc) - cert_u);
-        float fl = Fu, il = sqrtf(fmaxf(is - ic, 0.f));
+        if (act && (a.cone == CONE_EQ || !(ev[2] > 0.f))) d_lb = fmaxf(d_lb, Fu + ev[0] - cert_u);
+        float fl = Fu, il = sqrtf(fmaxf(ev[1], 0.f));
         // save ubar (the warm-start chain continues from it)
         for (int c0 = 0; c0 < NPAD; c0 += 16) {
-          uint32_t x[16];
-          tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+          uint32_t x[8];
+          C.ld8(C.rX, c0, x);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c0 + i < n) a.save[im(tile, n, c0 + i, tid)] = __uint_as_float(x[i]);
+          for (int i = 0; i < 8; ++i)
+            if (c0 + h8 + i < n) a.save[im(tile, n, c0 + h8 + i, lane)] = __uint_as_float(x[i]);
         }
         if (a.want_last) {
           if (a.fast) {  // ubar(lambda^k): extra inner solve at lambda^k from ubar^k
@@ -687,13 +721,13 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
             if (act && (a.cone == CONE_EQ || !lneg)) d_lb = fmaxf(d_lb, fl + lag - cert_l);
           }
           for (int c0 = 0; c0 < NPAD; c0 += 16) {
-            uint32_t x[16];
-            tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+            uint32_t x[8];
+            C.ld8(C.rX, c0, x);
             tc::tmem_ld_wait();
             if (!act) continue;
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (c0 + i < n) a.xlT[im(tile, n, c0 + i, tid)] = __uint_as_float(x[i]);
+            for (int i = 0; i < 8; ++i)
+              if (c0 + h8 + i < n) a.xlT[im(tile, n, c0 + h8 + i, lane)] = __uint_as_float(x[i]);
           }
           if (act) {
             f_l = fl;
@@ -702,13 +736,13 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
         }
         if (a.want_avg) {  // x_avg = usum / S, evaluated in region X
           for (int c0 = 0; c0 < NPAD; c0 += 16) {
-            uint32_t v[16];
+            uint32_t v[8];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int col = c0 + i;
-              v[i] = __float_as_uint(col < n && S > 0.0 ? (float)(a.usum[im(tile, n, col, tid)] / S) : 0.f);
+            for (int i = 0; i < 8; ++i) {
+              const int col = c0 + h8 + i;
+              v[i] = __float_as_uint(col < n && S > 0.0 ? (float)(a.usum[im(tile, n, col, lane)] / S) : 0.f);
             }
-            tc::tmem_st16(C.tm + C.lane_off + C.rX + c0, v);
+            C.st8(C.rX, c0, v);
           }
           tc::tmem_st_wait();
           C.operand_from(C.rX);
@@ -720,25 +754,25 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
           if (act) {
             f_a = fa;
             i_a = sqrtf(fmaxf(inf2, 0.f));
-            for (int i0 = 0; i0 < n; i0 += 16) {
+            for (int i0 = 16 * half; i0 < n; i0 += 32) {
               float us[16];
 #pragma unroll
-              for (int i = 0; i < 16; ++i) us[i] = i0 + i < n ? __ldcg(a.usum + im(tile, n, i0 + i, tid)) : 0.f;
+              for (int i = 0; i < 16; ++i) us[i] = i0 + i < n ? __ldcg(a.usum + im(tile, n, i0 + i, lane)) : 0.f;
 #pragma unroll
               for (int i = 0; i < 16; ++i)
-                if (i0 + i < n) a.xaT[im(tile, n, i0 + i, tid)] = (float)(us[i] / S);
+                if (i0 + i < n) a.xaT[im(tile, n, i0 + i, lane)] = (float)(us[i] / S);
             }
           }
         }
         // restore ubar into region X
         for (int c0 = 0; c0 < NPAD; c0 += 16) {
-          uint32_t v[16];
+          uint32_t v[8];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int col = c0 + i;
-            v[i] = __float_as_uint(col < n ? a.save[im(tile, n, col, tid)] : 0.f);
+          for (int i = 0; i < 8; ++i) {
+            const int col = c0 + h8 + i;
+            v[i] = __float_as_uint(col < n ? a.save[im(tile, n, col, lane)] : 0.f);
           }
-          tc::tmem_st16(C.tm + C.lane_off + C.rX + c0, v);
+          C.st8(C.rX, c0, v);
         }
         C.sync_async();
         if (act) {
@@ -760,15 +794,15 @@ __global__ void __launch_bounds__(TM, 1) k_tc_solve(TcArgs a) {
     }
     // ---- per-lane results and warm-start state
     for (int c0 = 0; c0 < NPAD; c0 += 16) {
-      uint32_t x[16];
-      tc::tmem_ld16(C.tm + C.lane_off + C.rX + c0, x);
+      uint32_t x[8];
+      C.ld8(C.rX, c0, x);
       tc::tmem_ld_wait();
       if (!valid) continue;
 #pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (c0 + i < n) a.xsT[im(tile, n, c0 + i, tid)] = __uint_as_float(x[i]);
+      for (int i = 0; i < 8; ++i)
+        if (c0 + h8 + i < n) a.xsT[im(tile, n, c0 + h8 + i, lane)] = __uint_as_float(x[i]);
     }
-    if (valid) {
+    if (valid && half == 0) {
       if (a.outer_fixed > 0 && status == ST_NOT_CONVERGED) status = ST_OK;
       DevResult r;
       r.status = status;
@@ -989,7 +1023,7 @@ dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_r
   a.next = W->next; a.err = W->err;
   DQ_CK(cudaFuncSetAttribute(k_tc_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = std::min(W->ntiles, ctx->num_sms);
-  k_tc_solve<<<grid, TM, smem, st>>>(a);
+  k_tc_solve<<<grid, TC_THREADS, smem, st>>>(a);
   ++ctx->launches;
   DQ_CK(cudaGetLastError());
   // warm-start state and outputs back to row-major
