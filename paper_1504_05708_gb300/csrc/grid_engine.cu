@@ -531,15 +531,15 @@ struct GridWs {
   int blocks = 0;
   // single-pass (v2) layout: packed upper triangle of Q and partial sums
   void* v2mem = nullptr;
-  float* Qp = nullptr;
-  long long* qoff = nullptr;
+  float4* Qb = nullptr;           // blocked packed upper triangle (float4 per column of 4 rows)
+  long long* boff = nullptr;      // n/4 block offsets (float4 units)
   int* rows = nullptr;       // qrow (nQ + 1) then grow (nG + 1)
   float* dotQ = nullptr;
   float4* parts = nullptr;
   int v2_ctas = 0;
   bool v2_ready = false;
-  const void* v2_src = nullptr;  // the matrix packed into Qp (Q, or H below)
-  std::vector<long long> hoff;  // host copy of the packed-row offsets
+  const void* v2_src = nullptr;  // the matrix packed into Qb (Q, or H below)
+  std::vector<long long> hoff;  // host copy of the block offsets (n/4 + 1 entries)
   // K = {0}, rho > 0: H = Q + rho G'G, so the inner gradient is one product
   void* H = nullptr;
   double H_rho = NAN;
@@ -722,23 +722,23 @@ struct GridRun {
   }
 
   // ---- single-pass iteration (grid_v2.cuh): setup and launch
-  static constexpr double kV2GWeight = 1.0;
+  static constexpr double kV2GWeight = 0.8;  // best of a sweep at n = 20000, p = 10000 (0.6 .. 1.25)
   bool use_v2 = false;
   int v2_nQ = 0, v2_nG = 0, v2_npt = 0;
   size_t v2_smem = 0;
 
   dq_status v2_setup(bool aug) {
-    const int n4 = n / 4, B2 = P->ctx->num_sms;
+    const int n4 = n / 4, nb = n4, B2 = P->ctx->num_sms;
     if (!W->v2_ready) {
-      W->hoff.resize(n + 1);
+      W->hoff.resize(nb + 1);
       long long acc = 0;
-      for (int i = 0; i < n; ++i) {
-        W->hoff[i] = acc;
-        acc += n - (i & ~3);
+      for (int bl = 0; bl < nb; ++bl) {
+        W->hoff[bl] = acc;
+        acc += n - 4 * bl;
       }
-      W->hoff[n] = acc;
+      W->hoff[nb] = acc;
       auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-      const size_t bQ = a256((size_t)acc * 4), bO = a256((size_t)n * 8), bR = a256((size_t)(B2 + 2) * 4),
+      const size_t bQ = a256((size_t)acc * 16), bO = a256((size_t)nb * 8), bR = a256((size_t)(B2 + 2) * 4),
                    bD = a256((size_t)n * 4), bP = a256((size_t)B2 * n4 * 16);
       if (cudaMalloc(&W->v2mem, bQ + bO + bR + bD + bP) != cudaSuccess) {
         cudaGetLastError();
@@ -746,47 +746,38 @@ struct GridRun {
         return DQ_ERR_NOMEM;
       }
       char* b = (char*)W->v2mem;
-      W->Qp = (float*)b;
-      W->qoff = (long long*)(b + bQ);
+      W->Qb = (float4*)b;
+      W->boff = (long long*)(b + bQ);
       W->rows = (int*)(b + bQ + bO);
       W->dotQ = (float*)(b + bQ + bO + bR);
       W->parts = (float4*)(b + bQ + bO + bR + bD);
-      DQ_CK(cudaMemcpyAsync(W->qoff, W->hoff.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st));
+      DQ_CK(cudaMemcpyAsync(W->boff, W->hoff.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, st));
       W->v2_ready = true;
     }
     if (W->v2_src != (const void*)Qm()) {  // (re)pack the matrix of the inner products
-      k_pack_upper<<<std::min(n, 8192), 256, 0, st>>>((const float*)Qm(), n, W->qoff, W->Qp);
+      k_pack_qblocks<<<std::min(nb, 8192), 256, 0, st>>>((const float*)Qm(), n, W->boff, W->Qb);
       ++P->ctx->launches;
       DQ_CK(cudaGetLastError());
       W->v2_src = (const void*)Qm();
     }
-    // CTA roles in proportion to the bytes each matrix contributes
-    // CTA roles in proportion to the cost of each matrix: a G row costs two passes over
-    // shared memory (dot, then the update once w_j is known) and a barrier, so its bytes
-    // weigh g_weight times a packed Q row's (DQ_V2_GWEIGHT overrides the default)
+    // CTA roles in proportion to the cost of each matrix's bytes: a G row costs two
+    // passes over shared memory (dot, then the update once w_j is known) and a
+    // barrier; a Q block shares its waits and reductions among four rows.  G bytes
+    // weigh g_weight times packed Q bytes (DQ_V2_GWEIGHT overrides the default).
     const char* gw_env = getenv("DQ_V2_GWEIGHT");
     const double g_weight = gw_env ? atof(gw_env) : kV2GWeight;
-    const double bq = double(W->hoff[n]), bg = aug ? g_weight * double(p) * n : 0.0;
+    const double bq = 4.0 * double(W->hoff[nb]), bg = aug ? g_weight * double(p) * n : 0.0;
     int nQ = aug && p > 0 ? (int)lround(B2 * bq / (bq + bg)) : B2;
     nQ = std::max(1, std::min(nQ, aug && p > 0 ? B2 - 1 : B2));
     const int nG = aug && p > 0 ? B2 - nQ : 0;
-    std::vector<int> rows(nQ + 1 + nG + 1);
-    rows[0] = 0;
-    int r = 0, maxq = 0;
-    for (int c = 1; c < nQ; ++c) {
-      const double target = bq * c / nQ;
-      while (r < n && double(W->hoff[r]) < target) ++r;
-      rows[c] = r;
-    }
-    rows[nQ] = n;
-    for (int c = 0; c < nQ; ++c) maxq = std::max(maxq, rows[c + 1] - rows[c]);
-    for (int c = 0; c <= nG; ++c) rows[nQ + 1 + c] = (int)((long long)p * c / std::max(nG, 1));
-    DQ_CK(cudaMemcpyAsync(W->rows, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice, st));
+    std::vector<int> grow(nG + 1);  // contiguous G-row ranges
+    for (int c = 0; c <= nG; ++c) grow[c] = (int)((long long)p * c / std::max(nG, 1));
+    DQ_CK(cudaMemcpyAsync(W->rows, grow.data(), grow.size() * 4, cudaMemcpyHostToDevice, st));
     v2_nQ = nQ;
     v2_nG = nG;
     v2_npt = std::max(2, ((n4 + V2_CONS - 1) / V2_CONS + 1) / 2 * 2);
-    (void)maxq;  // Q rows are dealt round-robin: each Q-CTA holds x_i of ceil(n / nQ) rows
-    const size_t xs_len = std::max<size_t>((n + nQ - 1) / nQ, nG > 0 ? (size_t)(p + nG - 1) / nG : 0) + 1;
+    // xs: the four x of each of a Q-CTA's blocks (blocks dealt round-robin), or a G-CTA's row constants
+    const size_t xs_len = std::max<size_t>(4 * (size_t)((nb + nQ - 1) / nQ), nG > 0 ? (size_t)(p + nG - 1) / nG : 0) + 4;
     v2_smem = (size_t)V2_STAGES * V2_CH4 * 16 + xs_len * 4 + 256;
     return DQ_OK;
   }
@@ -916,14 +907,15 @@ struct GridRun {
             V2Args A;
             memset(&A, 0, sizeof(A));
             A.n = n; A.p = p; A.n4 = n / 4; A.nQ = v2_nQ; A.nG = v2_nG;
-            A.qrow = W->rows; A.grow = W->rows + v2_nQ + 1; A.qoff = W->qoff; A.Qp = W->Qp; A.G = G();
+            A.grow = W->rows; A.boff = W->boff; A.Qb = W->Qb; A.G = G();
             A.x1 = v(X[sx]); A.x2 = v(X[sxp]); A.qx1 = v(QX[sx]); A.qx2 = v(QX[sxp]);
             A.tn = aug ? v(W->tn) : nullptr; A.addv = aug ? q() : v(W->c); A.lb = lb(); A.ub = ub();
             A.gx1 = v(GX[sx]); A.mu = mu; A.g = g();
             A.beta_prev = (float)beta; A.beta_next = (float)bnext; A.L = (float)LL; A.rho = (float)rho; A.cone = cone;
             A.xout = v(X[sn]); A.gxout = v(GX[sn]); A.dotQ = W->dotQ; A.partials = W->parts; A.done = dn;
             A.err = &W->ctrl->wait_err;
-            const double bytes = 4.0 * (double(W->hoff[n]) + (aug ? double(p) * n : 0.0) + 10.0 * n + (aug ? 4.0 * p : 0));
+            const double bytes = 4.0 * (4.0 * double(W->hoff[n / 4]) + (aug ? double(p) * n : 0.0) + 10.0 * n +
+                                        (aug ? 4.0 * p : 0));
             if (P->ctx->profile) {
               while ((int)W->evpool.size() < evn + 2) {
                 cudaEvent_t ev;
