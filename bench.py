@@ -36,6 +36,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "QP solves/s at eps=1e-3"
+# DRAM bytes (read + write) per algorithmic byte of the large-dense kernels, each from one ncu
+# capture (profiles/k_v2_pass_large_dense.md at n = 12000, profiles/k_rows_large_dense.md at
+# n = 8192), applied to the full-size launches: both kernels read every matrix element once, so
+# traffic grows in proportion to the bytes a launch processes
+TRAFFIC_RATIO = {"k_v2_pass": 1.0056, "k_rows": 1.0115}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -105,6 +110,20 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def replica_rate(ms_local, steps, world, device=None):
+    """Replicas only: every rank times its own `steps` solves; the job's time is the
+    maximum over ranks and its rate counts the solves of all ranks (weak scaling).
+    Returns (ms_max, solves_per_s).  No data crosses ranks, only this one scalar."""
+    ms_max = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max / 1e3)
 
 
 # ------------------------------------------------------------------ workloads
@@ -204,13 +223,7 @@ def run_gpu(args):
     clk = clocks.stop()
     st = ctx.stats(reset=True)
     ctx.profile(False)
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max, value = replica_rate(ms, args.steps, world, device="cuda")
 
     # end to end through the C ABI from pinned host memory
     e2e = None
@@ -249,7 +262,11 @@ def run_gpu(args):
                                 if single_pass else "k_rows<float> inner-iteration GEMV"),
                      "bound": "hbm", "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "traffic": None,
+                     "frac": (achieved / peaks["hbm_gbs"]) if achieved else None,
+                     "traffic": (st["gemv_bytes"] / st["gemv_launches"] *
+                                 TRAFFIC_RATIO["k_v2_pass" if single_pass else "k_rows"])
+                     if st["gemv_launches"] else None,
+                     "traffic_unit": "bytes per launch (scaled from a smaller capture)",
                      "peak_kind": kind, "launches_timed": st["gemv_launches"],
                      "gemv_share_of_step": (st["gemv_ms"] / ms) if ms > 0 else None},
         "gpu_launches": st["launches"],
@@ -488,7 +505,12 @@ def run_uneven(args):
                       {"count": count, "n": "U{16..512}", "p": "n/2", "algs": "DGM/DFGM/ADGM/ADFGM", "eps": 1e-3,
                        "autotuned": {"threads": tune[0], "smem_cap": tune[1]}, "graph": True,
                        "l2": "5.4 GB of matrices, larger than L2"}, clk, st, {
-                          "solve": {"converged": conv, "inner_iters_mean": float(inner.mean())},
+                          "solve": {"converged": conv, "inner_iters_mean": float(inner.mean()),
+                                    "inner_iters_p99": float(np.percentile(inner, 99)),
+                                    "inner_iters_max": float(inner.max()),
+                                    "n_of_max": int(nn[int(np.argmax(inner))]),
+                                    "work_share_top1pct": float(np.sort(inner * nn * nn)[::-1][:max(1, count // 100)].sum()
+                                                                / max((inner * nn * nn).sum(), 1.0))},
                           "roofline": {"kernel": "cta_solve_kernel<float> (persistent)", "bound": "alu",
                                        "achieved": tflops, "peak": FP32_FFMA_TFLOPS, "unit": "TFLOP/s",
                                        "frac": tflops / FP32_FFMA_TFLOPS, "traffic": None,
