@@ -133,7 +133,7 @@ class LargeDense:
 
     name = "large_dense_n20000_p10000_fp32_adfgm"
 
-    def __init__(self, args, device):
+    def __init__(self, args, device, equality=False):
         import torch
 
         import workloads as W
@@ -141,7 +141,10 @@ class LargeDense:
         self.alg = args.alg
         self.eps = args.eps
         self.dev = device
-        d = W.large_dense(n=self.n, p=self.p, seed=1, device=f"cuda:{device}")
+        self.equality = equality
+        if equality:
+            self.name = "large_dense_eq_n20000_p10000_fp32_adfgm_hessian"
+        d = W.large_dense(n=self.n, p=self.p, seed=1, device=f"cuda:{device}", equality=equality)
         self.d = d
         self.lmin = d["lmin_Q"]
         self.eps_in = args.eps_in
@@ -156,7 +159,8 @@ class LargeDense:
 
     def step_device(self, D, ctx, outs):
         d = self.d
-        P = D.Problem(ctx, d["Q"], d["q"], d["G"], d["g"], d["lb"], d["ub"], prec=D.FP32, lmin_Q=self.lmin)
+        P = D.Problem(ctx, d["Q"], d["q"], d["G"], d["g"], d["lb"], d["ub"], prec=D.FP32, lmin_Q=self.lmin,
+                      cone=D.CONE_EQ if self.equality else D.CONE_INEQ)
         res = P.solve(self.opts(D), device_out=outs)
         P.close()
         return res
@@ -169,7 +173,8 @@ class LargeDense:
 
     def step_host(self, D, ctx):
         h = self.host_inputs()
-        P = D.Problem(ctx, h["Q"], h["q"], h["G"], h["g"], h["lb"], h["ub"], prec=D.FP32, lmin_Q=self.lmin)
+        P = D.Problem(ctx, h["Q"], h["q"], h["G"], h["g"], h["lb"], h["ub"], prec=D.FP32, lmin_Q=self.lmin,
+                      cone=D.CONE_EQ if self.equality else D.CONE_INEQ)
         out = P.solve(self.opts(D))
         P.close()
         return out
@@ -191,7 +196,7 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-    wl = LargeDense(args, local)
+    wl = LargeDense(args, local, equality=args.workload == "eq")
     stream = torch.cuda.current_stream()
     ctx = D.Context(local, stream)
     n, p = wl.n, wl.p
@@ -252,13 +257,16 @@ def run_gpu(args):
         "config": {"workload": wl.name, "n": n, "p": p, "alg": wl.alg, "eps": wl.eps,
                    "eps_in": wl.eps_in, "outputs": "last+average", "check_every": wl.check_every,
                    "inner_check_every": wl.inner_check_every,
-                   "l2": "inputs larger than L2 (packed Q 0.8 GB, G 0.8 GB per inner iteration)",
+                   "l2": ("inputs larger than L2 (packed H = Q + rho G'G 0.8 GB per inner iteration)"
+                          if wl.equality else "inputs larger than L2 (packed Q 0.8 GB, G 0.8 GB per inner iteration)"),
+                   "cone": "K={0}, Hessian mode (H built in every step)" if wl.equality else "K=R^p_-",
                    "parallelism": f"replicas{world}"},
         "solve": {"status": r0.status, "outer_iters": r0.outer_iters, "inner_iters_mean": inner,
                   "f_last": r0.f_last, "infeas_last": r0.infeas_last, "f_avg": r0.f_avg,
                   "infeas_avg": r0.infeas_avg, "d_lb": r0.d_lb, "converged_last": r0.converged_last,
                   "converged_avg": r0.converged_avg},
-        "roofline": {"kernel": ("k_v2_pass<float> single-pass inner iteration (packed Q, one read of G)"
+        "roofline": {"kernel": (("k_v2_pass<float> single-pass inner iteration (packed H)" if wl.equality else
+                                 "k_v2_pass<float> single-pass inner iteration (packed Q, one read of G)")
                                 if single_pass else "k_rows<float> inner-iteration GEMV"),
                      "bound": "hbm", "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -291,7 +299,8 @@ def cpu_baseline_large(wl, inner_per_solve, outer_per_solve, budget_s):
     import oracle as O
     d = wl.d
     qp = O.QP(d["Q"].double().cpu().numpy(), d["q"].double().cpu().numpy(), d["G"].double().cpu().numpy(),
-              d["g"].double().cpu().numpy(), d["lb"].double().cpu().numpy(), d["ub"].double().cpu().numpy())
+              d["g"].double().cpu().numpy(), d["lb"].double().cpu().numpy(), d["ub"].double().cpu().numpy(),
+              cone=O.CONE_EQ if getattr(wl, "equality", False) else O.CONE_INEQ)
     mu = np.zeros(wl.p)
     x0 = np.zeros(wl.n)
     rho = 1.0 / 3.0
@@ -479,6 +488,7 @@ def run_uneven(args):
         on += d["n"]
         op += d["p"]
     tune = D.autotune(probs, ops, sample=256)
+    peaks, kind = load_peaks()
     ms, clk, st, res = _timed(ctx, stream, lambda: D.solve_many(probs, ops, device_outs=douts), args.steps, args.warmup)
     rs = res[-1]
     nn = np.array([d["n"] for d in insts], float)
@@ -487,6 +497,12 @@ def run_uneven(args):
     inner = np.array([r.inner_iters for r in rs], float)
     flops = float(np.sum(inner * (2 * nn * nn + np.where(aug, 4 * nn * pp, 0.0))))
     tflops = flops / (ms / args.steps / 1e3) / 1e12
+    # matrix bytes the algorithm streams: Q (and G, G' when rho > 0) per inner iteration, G and
+    # G' once per outer iteration when rho = 0 (the batch's 5.4 GB of matrices exceed L2)
+    outer = np.array([r.outer_iters for r in rs], float)
+    mbytes = float(np.sum(inner * 4 * (nn * nn + np.where(aug, 2 * nn * pp, 0.0)) +
+                          outer * np.where(aug, 0.0, 8 * nn * pp)))
+    gbs = mbytes / (ms / args.steps / 1e3) / 1e9
     conv = sum(1 for r in rs if r.status == 0)
     # CPU baseline: the FP64 oracle on a sample of the same instances, all host cores
     sample = list(range(0, count, max(1, count // 400)))
@@ -511,10 +527,14 @@ def run_uneven(args):
                                     "n_of_max": int(nn[int(np.argmax(inner))]),
                                     "work_share_top1pct": float(np.sort(inner * nn * nn)[::-1][:max(1, count // 100)].sum()
                                                                 / max((inner * nn * nn).sum(), 1.0))},
-                          "roofline": {"kernel": "cta_solve_kernel<float> (persistent)", "bound": "alu",
-                                       "achieved": tflops, "peak": FP32_FFMA_TFLOPS, "unit": "TFLOP/s",
-                                       "frac": tflops / FP32_FFMA_TFLOPS, "traffic": None,
-                                       "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                          "roofline": {"kernel": "cta_solve_kernel<float> (persistent)", "bound": "hbm",
+                                       "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                       "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_kind": kind,
+                                       "note": "matrix bytes streamed per iteration by the algorithm; instances "
+                                               "whose matrices fit shared memory read them there",
+                                       "alu": {"achieved": tflops, "peak": FP32_FFMA_TFLOPS, "unit": "TFLOP/s",
+                                               "frac": tflops / FP32_FFMA_TFLOPS,
+                                               "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}},
                           "e2e": None,
                           "cpu_baseline": {"value": cpu_v * mean_cost, "unit": "solves/s", "cores": cores, "kind": "oracle",
                                            "sample": f"{done} of {len(sample)} sampled instances solved by the FP64 oracle on "
@@ -713,7 +733,7 @@ def run_served(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="large", choices=["large", "small", "uneven", "mpc", "served"])
+    ap.add_argument("--workload", default="large", choices=["large", "eq", "small", "uneven", "mpc", "served"])
     ap.add_argument("--count", type=int, default=None)
     ap.add_argument("--rate", type=float, default=20000.0)
     ap.add_argument("--duration", type=float, default=0.5)

@@ -408,49 +408,66 @@ __global__ void k_lz_next(T* v, T* vp, const T* w, int n, const Ctrl* ctrl, int 
 }
 
 // H = Q + rho G'G for the equality-constrained augmented Lagrangian (K = {0}:
-// grad_x L_rho(x, mu) = (Q + rho G'G) x + q + G'(mu + rho g), Sec. 2).  Both
-// factors are row slices of G (p x n): a 64 x 64 tile of H per block, 256
-// threads with 4 x 4 outputs each, the p rows in steps of 16 through shared
-// memory, one accumulator per output in the element type.
+// grad_x L_rho(x, mu) = (Q + rho G'G) x + q + G'(mu + rho g), Sec. 2).  G'G is
+// symmetric, so only the 128 x 128 tiles (I, K) with K >= I are computed and
+// the off-diagonal ones are written twice.  Both factors are row slices of G
+// (p x n, coalesced 16-byte loads); 256 threads with 8 x 8 outputs each; the
+// p rows in steps of 8 through double-buffered shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ G, const T* __restrict__ Q, int n, int p, T rho,
                                               T* __restrict__ H) {
-  __shared__ __align__(16) T As[16][64], Bs[16][64];
-  const int i0 = blockIdx.y * 64, k0 = blockIdx.x * 64;
+  constexpr int TB = 128, KS = 8;
+  const int I = blockIdx.y, K = blockIdx.x;
+  if (K < I) return;
+  __shared__ __align__(16) T As[2][KS][TB], Bs[2][KS][TB];
+  const int i0 = I * TB, k0 = K * TB;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[4][4];
+  T acc[8][8];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 8; ++u)
 #pragma unroll
-    for (int w = 0; w < 4; ++w) acc[u][w] = T(0);
-  for (int j0 = 0; j0 < p; j0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-      const int r = e >> 6, c = e & 63, j = j0 + r;
-      As[r][c] = (j < p && i0 + c < n) ? G[(size_t)j * n + i0 + c] : T(0);
-      Bs[r][c] = (j < p && k0 + c < n) ? G[(size_t)j * n + k0 + c] : T(0);
+    for (int w = 0; w < 8; ++w) acc[u][w] = T(0);
+  // loader: thread -> (row r of the 8, 4 consecutive columns)
+  const int lr = threadIdx.x >> 5, lc = (threadIdx.x & 31) * 4;
+  auto load = [&](int buf, int j0) {
+    const int j = j0 + lr;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int ci = i0 + lc + u, ck = k0 + lc + u;
+      As[buf][lr][lc + u] = (j < p && ci < n) ? G[(size_t)j * n + ci] : T(0);
+      Bs[buf][lr][lc + u] = (j < p && ck < n) ? G[(size_t)j * n + ck] : T(0);
     }
-    __syncthreads();
+  };
+  load(0, 0);
+  __syncthreads();
+  int buf = 0;
+  for (int j0 = 0; j0 < p; j0 += KS) {
+    if (j0 + KS < p) load(buf ^ 1, j0 + KS);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      T a[4], b[4];
+    for (int r = 0; r < KS; ++r) {
+      T a[8], b[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = As[r][ty * 4 + u];
-        b[u] = Bs[r][tx * 4 + u];
+      for (int u = 0; u < 8; ++u) {
+        a[u] = As[buf][r][ty * 8 + u];
+        b[u] = Bs[buf][r][tx * 8 + u];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int w = 0; w < 4; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
+        for (int w = 0; w < 8; ++w) acc[u][w] = fma(a[u], b[w], acc[u][w]);
     }
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 8; ++u)
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      const int i = i0 + ty * 4 + u, k = k0 + tx * 4 + w;
-      if (i < n && k < n) H[(size_t)i * n + k] = Q[(size_t)i * n + k] + rho * acc[u][w];
+    for (int w = 0; w < 8; ++w) {
+      const int i = i0 + ty * 8 + u, k = k0 + tx * 8 + w;
+      if (i < n && k < n) {
+        H[(size_t)i * n + k] = Q[(size_t)i * n + k] + rho * acc[u][w];
+        if (K > I) H[(size_t)k * n + i] = Q[(size_t)k * n + i] + rho * acc[u][w];
+      }
     }
 }
 
@@ -1071,7 +1088,7 @@ struct GridRun {
       }
       DQ_CK(cudaMemsetAsync(W->zp, 0, (size_t)std::max(p, 1) * esz, st));
     }
-    const dim3 grid((n + 63) / 64, (n + 63) / 64);
+    const dim3 grid((n + 127) / 128, (n + 127) / 128);  // blocks below the diagonal return at once
     k_gram<T><<<grid, 256, 0, st>>>(G(), Q(), n, p, T(rho), (T*)W->H);
     ++P->ctx->launches;
     DQ_CK(cudaGetLastError());

@@ -344,8 +344,20 @@ __global__ void __launch_bounds__(V2R_COLS* V2R_GROUPS) k_v2_reduce(const float4
   for (int which = 0; which < (tnout ? 2 : 1); ++which) {
     const int c0 = which == 0 ? 0 : nQ, c1 = which == 0 ? nQ : nQ + nG;
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f), e = s;
-    if (in)
-      for (int cc = c0 + gi; cc < c1; cc += V2R_GROUPS) v2r_kahan(s, e, partials[(size_t)cc * n4 + c4]);
+    if (in) {
+      int cc = c0 + gi;
+      for (; cc + 3 * V2R_GROUPS < c1; cc += 4 * V2R_GROUPS) {  // four loads in flight, then the sums in order
+        const float4 v0 = __ldcg(partials + (size_t)cc * n4 + c4);
+        const float4 v1 = __ldcg(partials + (size_t)(cc + V2R_GROUPS) * n4 + c4);
+        const float4 v2 = __ldcg(partials + (size_t)(cc + 2 * V2R_GROUPS) * n4 + c4);
+        const float4 v3 = __ldcg(partials + (size_t)(cc + 3 * V2R_GROUPS) * n4 + c4);
+        v2r_kahan(s, e, v0);
+        v2r_kahan(s, e, v1);
+        v2r_kahan(s, e, v2);
+        v2r_kahan(s, e, v3);
+      }
+      for (; cc < c1; cc += V2R_GROUPS) v2r_kahan(s, e, __ldcg(partials + (size_t)cc * n4 + c4));
+    }
     sh[0][gi][col] = s;
     sh[1][gi][col] = make_float4(-e.x, -e.y, -e.z, -e.w);
     __syncthreads();

@@ -84,11 +84,13 @@ def single_dense(n=50, p=25, seed=0, lam_lo=1.0, lam_hi=100.0, g_scale=1.0, g_of
                     {"kind": "single_dense", "seed": seed})
 
 
-def large_dense(n=20000, p=10000, seed=1, device="cpu", dtype=None):
+def large_dense(n=20000, p=10000, seed=1, device="cpu", dtype=None, equality=False):
     """Large dense QP, Q = M'M/n + 0.01 I (lambda_min(Q) >= 0.01 by construction).
 
     Built with torch so the full-size case can be drawn directly in device
-    memory; returns a dict of torch tensors (Q, q, G, g, lb, ub) plus lmin_Q."""
+    memory; returns a dict of torch tensors (Q, q, G, g, lb, ub) plus lmin_Q.
+    equality=True: g = -G u0 with u0 ~ U[-1/2, 1/2]^n, so G u + g = 0 has a
+    solution inside the box (K = {0})."""
     import torch
 
     dtype = dtype or torch.float32
@@ -103,6 +105,9 @@ def large_dense(n=20000, p=10000, seed=1, device="cpu", dtype=None):
     q = torch.randn(n, generator=gen, device=device, dtype=work)
     G = torch.randn(p, n, generator=gen, device=device, dtype=work) / (n ** 0.5)
     g = -torch.randn(p, generator=gen, device=device, dtype=work).abs() - 0.1
+    if equality:
+        u0 = torch.rand(n, generator=gen, device=device, dtype=work) - 0.5
+        g = -(G @ u0)
     lb = -torch.ones(n, device=device, dtype=work)
     ub = torch.ones(n, device=device, dtype=work)
     out = {k: v.to(dtype).contiguous() for k, v in dict(Q=Q, q=q, G=G, g=g, lb=lb, ub=ub).items()}
