@@ -64,7 +64,7 @@ class _Opts(ctypes.Structure):
                 ("max_inner", ctypes.c_int), ("outer_fixed", ctypes.c_int),
                 ("eps_out", ctypes.c_double), ("outer_check_every", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("want_last", ctypes.c_int),
-                ("want_avg", ctypes.c_int)]
+                ("want_avg", ctypes.c_int), ("inner_cert_step", ctypes.c_int)]
 
 
 class _Res(ctypes.Structure):
@@ -99,8 +99,10 @@ def _load():
             lib.orc_inner_cert.restype = d
             lib.orc_inner_cert.argtypes = [qpp, d, dp, dp, d, d]
             lib.orc_fom.restype = ctypes.c_int
+            lib.orc_step_cert.restype = d
+            lib.orc_step_cert.argtypes = [qpp, d, dp, dp, d, d, dp]
             lib.orc_fom.argtypes = [qpp, d, dp, d, d, ctypes.c_int, ctypes.c_int, d, ctypes.c_int,
-                                    ctypes.c_int, dp, dp, ctypes.c_int]
+                                    ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int]
             lib.orc_dfom.restype = ctypes.c_int
             lib.orc_dfom.argtypes = [qpp, P(_Opts), dp, dp, dp, dp, dp, P(_Res), dp, ctypes.c_int]
             lib.orc_power_lmax.restype = d
@@ -193,14 +195,26 @@ def inner_cert(qp: QP, rho: float, x, lam, LL: float, sigma: float) -> float:
     return _load().orc_inner_cert(ctypes.byref(qp._c()), rho, _dp(_f64(x)), _dp(lam), LL, sigma)
 
 
+def step_cert(qp: QP, rho: float, y, lam, LL: float, sigma: float):
+    """Bound on L_rho(x+, lam) - d_rho(lam) for x+ = [y - grad/L]_U from any step point y
+    (sigma > 0). Returns (bound, x+)."""
+    lam = _f64(lam) if qp.p else np.zeros(1)
+    xp = np.zeros(qp.n)
+    b = _load().orc_step_cert(ctypes.byref(qp._c()), rho, _dp(_f64(y)), _dp(lam), LL, sigma, _dp(xp))
+    return b, xp
+
+
 def fom(qp: QP, rho, mu, LL, sigma, x0, *, variant=INNER_AUTO, fixed=0, eps_in=1e-8,
-        check_every=1, max_inner=100000, phi_trace=0):
-    """Algorithm FOM on L_rho(., mu) over the box (Sec. 2.1). Returns (x, iters, phi[k])."""
+        check_every=1, max_inner=100000, phi_trace=0, cert_step=False):
+    """Algorithm FOM on L_rho(., mu) over the box (Sec. 2.1). Returns (x, iters, phi[k]).
+    cert_step: stop on the step certificate of y^k -> x^k (sigma > 0) instead of the
+    certificate at x^k."""
     x = _f64(x0).copy()
     mu = _f64(mu) if qp.p else np.zeros(1)
     tr = np.zeros(max(phi_trace, 1))
     k = _load().orc_fom(ctypes.byref(qp._c()), rho, _dp(mu), LL, sigma, variant, fixed, eps_in,
-                        check_every, max_inner, _dp(x), _dp(tr) if phi_trace else None, phi_trace)
+                        check_every, max_inner, int(cert_step), _dp(x),
+                        _dp(tr) if phi_trace else None, phi_trace)
     return x, k, tr[:min(k, phi_trace)] if phi_trace else None
 
 
@@ -265,7 +279,7 @@ class Result:
 def dfom(qp: QP, alg: int, c: Constants, *, inner_fixed=0, eps_in=1e-6, inner_check_every=1,
          max_inner=100000, outer_fixed=0, eps_out=1e-3, outer_check_every=1, max_outer=10000,
          want_last=True, want_avg=True, lambda0=None, x0=None, kd_literal=False,
-         inner_variant=INNER_AUTO, trace_cap=0) -> Result:
+         inner_variant=INNER_AUTO, trace_cap=0, inner_cert_step=False) -> Result:
     """Algorithm DFOM(d_rho, K_d) (Sec. 3) with both primal outputs (Sec. 4)."""
     o = _Opts()
     o.alg, o.rho, o.LL, o.sigma, o.Ld = alg, c.rho, c.LL, c.sigma, c.Ld
@@ -273,6 +287,7 @@ def dfom(qp: QP, alg: int, c: Constants, *, inner_fixed=0, eps_in=1e-6, inner_ch
     o.inner_fixed, o.eps_in, o.inner_check_every, o.max_inner = inner_fixed, eps_in, inner_check_every, max_inner
     o.outer_fixed, o.eps_out, o.outer_check_every, o.max_outer = outer_fixed, eps_out, outer_check_every, max_outer
     o.want_last, o.want_avg = int(want_last), int(want_avg)
+    o.inner_cert_step = int(inner_cert_step)
     n, p = qp.n, qp.p
     xl, xa, lam = np.zeros(n), np.zeros(n), np.zeros(max(p, 1))
     l0 = _f64(lambda0) if (lambda0 is not None and p) else None

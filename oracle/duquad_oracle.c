@@ -61,6 +61,7 @@ typedef struct {
   int outer_check_every;
   int max_outer;
   int want_last, want_avg;
+  int inner_cert_step; /* 1: stop on the step certificate (sigma > 0 only)   */
 } orc_opts;
 
 typedef struct {
@@ -251,6 +252,32 @@ double orc_inner_cert(const orc_qp *qp, double rho, const double *x, const doubl
   return lin + sq * kappa;
 }
 
+/* Step certificate: a bound for the iterate x+ = [y - grad phi(y)/L]_U that
+ * a gradient step from ANY point y (inside the box or not) produces,
+ *     phi(x+) - phi* <= ||g||^2 (1/(2 sigma) - 1/(2 L)),  g = L (y - x+),
+ * the proximal-gradient inequality for a sigma-strongly convex, L-smooth phi
+ * (the second half of the bound above, taken at the step point instead of at
+ * the iterate).  It needs only y and x+, which the inner step forms anyway,
+ * so an implementation can check it every iteration without another
+ * gradient.  Reading: any computable upper bound on L_rho(x, mu) - d_rho(mu)
+ * enforces eq. duquad_in; this one is defined for sigma > 0 only.
+ * xplus (optional) receives x+. */
+double orc_step_cert(const orc_qp *qp, double rho, const double *y, const double *lam,
+                     double LL, double sigma, double *xplus) {
+  int n = qp->n;
+  double *gr = malloc(sizeof(double) * n);
+  orc_grad_lagr(qp, rho, y, lam, gr);
+  double sq = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double xp = clampd(y[i] - gr[i] / LL, qp->lb[i], qp->ub[i]);
+    if (xplus) xplus[i] = xp;
+    double g = LL * (y[i] - xp);
+    sq += g * g;
+  }
+  free(gr);
+  return sq * (1.0 / (2.0 * sigma) - 1.0 / (2.0 * LL));
+}
+
 /* ---------------------------------------------------- Algorithm FOM (inner) */
 
 /* Algorithm FOM(phi, X) of Sec. 2.1 with phi = L_rho(., mu), X = U:
@@ -263,11 +290,13 @@ double orc_inner_cert(const orc_qp *qp, double rho, const double *x, const doubl
  * x holds x^0 on entry and the returned iterate on exit.
  * Stops after exactly inner_fixed iterations, or (certificate mode) at the
  * first k that is a multiple of inner_check_every with cert(x^k) <= eps_in, or
- * at max_inner.  Returns the number of iterations performed.
+ * at max_inner.  cert is orc_inner_cert at x^k, or (cert_step, sigma > 0)
+ * orc_step_cert of the step y^k -> x^k.  Returns the number of iterations
+ * performed.
  * phi_trace (optional, length >= cap) receives phi(x^k) for k = 1.. */
 int orc_fom(const orc_qp *qp, double rho, const double *mu, double LL, double sigma,
             int variant, int inner_fixed, double eps_in, int check_every, int max_inner,
-            double *x, double *phi_trace, int cap) {
+            int cert_step, double *x, double *phi_trace, int cap) {
   int n = qp->n;
   double *xp = malloc(sizeof(double) * n);  /* x^{k-1} */
   double *y = malloc(sizeof(double) * n);   /* y^k     */
@@ -284,6 +313,10 @@ int orc_fom(const orc_qp *qp, double rho, const double *mu, double LL, double si
     ++k;
     orc_grad_lagr(qp, rho, y, mu, gr);
     for (int i = 0; i < n; ++i) xn[i] = clampd(y[i] - gr[i] / LL, qp->lb[i], qp->ub[i]);
+    /* step certificate of y^k -> x^k, before y moves on */
+    double cstep = (cert_step && sigma > 0.0 && inner_fixed <= 0 && k % check_every == 0)
+                       ? orc_step_cert(qp, rho, y, mu, LL, sigma, NULL)
+                       : 0.0;
     double beta;
     if (variant == ORC_INNER_GM) {
       beta = 0.0;
@@ -300,7 +333,10 @@ int orc_fom(const orc_qp *qp, double rho, const double *mu, double LL, double si
     if (inner_fixed > 0) {
       if (k >= inner_fixed) break;
     } else {
-      if (k % check_every == 0 && orc_inner_cert(qp, rho, xn, mu, LL, sigma) <= eps_in) break;
+      if (k % check_every == 0) {
+        double cert = (cert_step && sigma > 0.0) ? cstep : orc_inner_cert(qp, rho, xn, mu, LL, sigma);
+        if (cert <= eps_in) break;
+      }
       if (k >= max_inner) break;
     }
   }
@@ -385,7 +421,7 @@ int orc_dfom(const orc_qp *qp, const orc_opts *o, const double *lambda0, const d
     ++k;
     /* step 1: inner solve at mu^k, warm start from ubar^{k-1} */
     int it = orc_fom(qp, rho, mu, o->LL, o->sigma, o->inner_variant, o->inner_fixed, o->eps_in,
-                     o->inner_check_every, o->max_inner, u, NULL, 0);
+                     o->inner_check_every, o->max_inner, o->inner_cert_step, u, NULL, 0);
     inner_total += it;
     /* step 2: inexact dual gradient and projected dual step */
     orc_dual_grad(qp, rho, u, mu, dg);
@@ -431,7 +467,8 @@ int orc_dfom(const orc_qp *qp, const orc_opts *o, const double *lambda0, const d
         memcpy(ul, u, sizeof(double) * n);
         if (fast) {
           int it2 = orc_fom(qp, rho, lam, o->LL, o->sigma, o->inner_variant, o->inner_fixed,
-                            o->eps_in, o->inner_check_every, o->max_inner, ul, NULL, 0);
+                            o->eps_in, o->inner_check_every, o->max_inner, o->inner_cert_step, ul,
+                            NULL, 0);
           inner_total += it2;
           if (lower_bound_valid(qp, o, lam)) {
             double lb = orc_lagrangian(qp, rho, ul, lam) - orc_inner_cert(qp, rho, ul, lam, o->LL, o->sigma);

@@ -553,6 +553,7 @@ struct GridWs {
   int* rows = nullptr;       // qrow (nQ + 1) then grow (nG + 1)
   float* dotQ = nullptr;
   float4* parts = nullptr;
+  float* cbuf = nullptr;          // step-certificate partials, two buffers of num_sms floats
   int v2_ctas = 0;
   bool v2_ready = false;
   const void* v2_src = nullptr;  // the matrix packed into Qb (Q, or H below)
@@ -756,8 +757,8 @@ struct GridRun {
       W->hoff[nb] = acc;
       auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
       const size_t bQ = a256((size_t)acc * 16), bO = a256((size_t)nb * 8), bR = a256((size_t)(B2 + 2) * 4),
-                   bD = a256((size_t)n * 4), bP = a256((size_t)B2 * n4 * 16);
-      if (cudaMalloc(&W->v2mem, bQ + bO + bR + bD + bP) != cudaSuccess) {
+                   bD = a256((size_t)n * 4), bP = a256((size_t)B2 * n4 * 16), bC = a256((size_t)2 * B2 * 4);
+      if (cudaMalloc(&W->v2mem, bQ + bO + bR + bD + bP + bC) != cudaSuccess) {
         cudaGetLastError();
         set_error("packed-Q allocation failed");
         return DQ_ERR_NOMEM;
@@ -768,6 +769,7 @@ struct GridRun {
       W->rows = (int*)(b + bQ + bO);
       W->dotQ = (float*)(b + bQ + bO + bR);
       W->parts = (float4*)(b + bQ + bO + bR + bD);
+      W->cbuf = (float*)(b + bQ + bO + bR + bD + bP);
       DQ_CK(cudaMemcpyAsync(W->boff, W->hoff.data(), (size_t)nb * 8, cudaMemcpyHostToDevice, st));
       W->v2_ready = true;
     }
@@ -911,6 +913,14 @@ struct GridRun {
       theta = t1;
       return bn;
     };
+    // Step certificate (sigma > 0, single-pass form): each launch bounds the
+    // iterate it makes from its own step, and the next launch stops the loop;
+    // the certificate costs no gradient at x^k and is checked every iteration
+    // (m only sets how often the host looks at the flag).
+    const char* sc_env = getenv("DQ_STEP_CERT");
+    const bool step_cert = use_v2 && fixed <= 0 && sigma > 0.0 && !(sc_env && atoi(sc_env) == 0);
+    const int nsm = P->ctx->num_sms;
+    const float ccoef = (float)(LL * LL * (0.5 / sigma - 0.5 / LL));
     while (k < kmax && kstop < 0) {
       // one chunk of up to m iterations, then (gap mode) the certificate
       const int kend = std::min(kmax, k + (fixed > 0 ? kmax : m));
@@ -929,8 +939,15 @@ struct GridRun {
             A.tn = aug ? v(W->tn) : nullptr; A.addv = aug ? q() : v(W->c); A.lb = lb(); A.ub = ub();
             A.gx1 = v(GX[sx]); A.mu = mu; A.g = g();
             A.beta_prev = (float)beta; A.beta_next = (float)bnext; A.L = (float)LL; A.rho = (float)rho; A.cone = cone;
-            A.xout = v(X[sn]); A.gxout = v(GX[sn]); A.dotQ = W->dotQ; A.partials = W->parts; A.done = dn;
+            A.xout = v(X[sn]); A.gxout = v(GX[sn]); A.dotQ = W->dotQ; A.partials = W->parts;
+            A.done = fixed > 0 ? nullptr : &W->ctrl->inner_done;
             A.err = &W->ctrl->wait_err;
+            if (step_cert) {
+              A.cpart = W->cbuf + (k & 1) * nsm;
+              A.cprev = k > 1 ? W->cbuf + ((k - 1) & 1) * nsm : nullptr;
+              A.ccoef = ccoef; A.eps_in = (float)eps_in; A.kprev = k - 1; A.kmax = kmax;
+              A.kstop = &W->ctrl->k_stop; A.cert = &W->ctrl->cert;
+            }
             const double bytes = 4.0 * (4.0 * double(W->hoff[n / 4]) + (aug ? double(p) * n : 0.0) + 10.0 * n +
                                         (aug ? 4.0 * p : 0));
             if (P->ctx->profile) {
@@ -981,7 +998,9 @@ struct GridRun {
       const int sc = slot_of(k);
       if (k % m == 0 || k >= kmax) {
         const T* add2 = nullptr;
-        if (aug) {  // gradient at x: G' [mu + rho (G x + g)]_+ (its own buffer: tn feeds the next pass)
+        if (step_cert) {
+          // the passes check the certificate themselves
+        } else if (aug) {  // gradient at x: G' [mu + rho (G x + g)]_+ (its own buffer: tn feeds the next pass)
           RowJob<T> J = job();
           J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->pw);
           J.vmode = VM_W; J.a0 = v(GX[sc]); J.a1 = v(GX[sc]); J.a2 = mu; J.a3 = g();
@@ -989,10 +1008,12 @@ struct GridRun {
           if ((e = rows<false>(J)) != cudaSuccess) break;
           add2 = v(W->pw);
         }
-        k_cert<T><<<eb, 512, 0, st>>>(v(X[sc]), v(QX[sc]), aug ? q() : v(W->c), add2, lb(), ub(), n, LL, sigma,
-                                       eps_in, k, kmax, W->partials, W->ctrl);
-        ++P->ctx->launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if (!step_cert) {
+          k_cert<T><<<eb, 512, 0, st>>>(v(X[sc]), v(QX[sc]), aug ? q() : v(W->c), add2, lb(), ub(), n, LL,
+                                         sigma, eps_in, k, kmax, W->partials, W->ctrl);
+          ++P->ctx->launches;
+          if ((e = cudaGetLastError()) != cudaSuccess) break;
+        }
         // publish the flag; look at the previous chunk's flag (one chunk of lag)
         cudaMemcpyAsync(&W->hctrl[chunk & 1], W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
         cudaEventRecord(W->ev[chunk & 1], st);
@@ -1003,6 +1024,12 @@ struct GridRun {
         }
         ++chunk;
       }
+    }
+    if (e == cudaSuccess && step_cert && k > 0) {  // the last iteration's certificate, if no launch read it
+      k_v2_final<<<1, 32, 0, st>>>(W->cbuf + (k & 1) * nsm, v2_nQ, ccoef, k, &W->ctrl->inner_done,
+                                   &W->ctrl->k_stop, &W->ctrl->cert);
+      ++P->ctx->launches;
+      e = cudaGetLastError();
     }
     if (e != cudaSuccess) {
       set_error("inner loop launch: %s", cudaGetErrorString(e));

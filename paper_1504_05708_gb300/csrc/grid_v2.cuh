@@ -52,8 +52,18 @@ struct V2Args {
   float* gxout;                       // G x^k
   float* dotQ;                        // row dots of the packed rows
   float4* partials;                   // (nQ + nG) x n4 (column-indexed)
-  const int* done;
+  int* done;                          // inner loop finished (set by an earlier launch, or below)
   int* err;                           // set to 1 when a bounded wait gave up
+  // step certificate (sigma > 0): this launch writes cpart[c] = sum over the
+  // x-slice of Q-CTA c of (y_j - x_j)^2; at its start every CTA adds the
+  // previous launch's cprev[0..nQ) in the same order, and stops the loop when
+  // ccoef * sum <= eps_in (or kprev >= kmax): CTA 0 records cert and kstop.
+  float* cpart;
+  const float* cprev;
+  float ccoef, eps_in;
+  int kprev, kmax;
+  int* kstop;
+  double* cert;
 };
 
 static constexpr int V2_CONS = 512;                 // threads (16 warps), all consumers
@@ -90,8 +100,29 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
   __shared__ __align__(8) uint64_t full[V2_STAGES], empty[V2_STAGES];
   __shared__ float4 sdot[V2_RB][V2_CONS / 32];
   __shared__ float sred[2][V2_CONS / 32];
-  if (a.done && *(volatile const int*)a.done) return;
+  __shared__ int s_stop;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (warp == 0) {  // loop control: done flag, or the step certificate of the previous launch
+    int stop = a.done ? *(volatile const int*)a.done : 0;
+    if (!stop && a.cprev) {
+      float v = 0.f;
+      for (int i = lane; i < a.nQ; i += 32) v += __ldcg(a.cprev + i);
+      v = v2_warp_sum(v);  // butterfly: the same bits in every lane and every CTA
+      const float ct = a.ccoef * v;
+      if (ct <= a.eps_in || a.kprev >= a.kmax) {
+        stop = 1;
+        if (blockIdx.x == 0 && lane == 0) {
+          *a.cert = (double)ct;
+          *a.kstop = a.kprev;
+          __threadfence();
+          *(volatile int*)a.done = 1;
+        }
+      }
+    }
+    if (lane == 0) s_stop = stop;
+  }
+  __syncthreads();
+  if (s_stop) return;
   const bool qcta = blockIdx.x < a.nQ;
   const int c = blockIdx.x, nQ = a.nQ, n = a.n, n4 = a.n4, nb = n4;
   const int klq = (n - 1) / V2_CH4;   // last chunk of every Q block
@@ -154,14 +185,15 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
   // ---------------- prologue: x^k = [y - grad(y)/L]_U for this thread's columns
   float xv[NQS], pv[NQS];  // G-CTA: float4 slot m is xv[4m..4m+3], pv[4m..4m+3]
   const float b = a.beta_prev;
-  auto step = [&](int j) {
+  auto step = [&](int j, float& y) {
     const float x = a.x1[j], xp = a.x2[j], qx = a.qx1[j], qxp = a.qx2[j];
-    const float y = x + b * (x - xp);
+    y = x + b * (x - xp);
     const float qy = qx + b * (qx - qxp);
     const float s = y - (qy + a.addv[j] + (a.tn ? a.tn[j] : 0.f)) / a.L;
     const float l = a.lb[j], h = a.ub[j];
     return s < l ? l : (s > h ? h : s);
   };
+  float csum = 0.f;  // step certificate: sum of (y_j - x_j)^2 over this CTA's x-slice
 #pragma unroll
   for (int m = 0; m < NQS; ++m) pv[m] = 0.f;
   if (qcta) {
@@ -171,8 +203,12 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
       const int j = t + V2_CONS * m;
       float o = 0.f;
       if (j < n) {
-        o = step(j);
-        if (j >= c * per && j < (c + 1) * per) a.xout[j] = o;
+        float y;
+        o = step(j, y);
+        if (j >= c * per && j < (c + 1) * per) {
+          a.xout[j] = o;
+          csum = fmaf(y - o, y - o, csum);
+        }
         const int blk = j >> 2;
         if (blk >= c && (blk - c) % nQ == 0) xs[((blk - c) / nQ) * 4 + (j & 3)] = o;
       }
@@ -183,13 +219,25 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
     for (int m = 0; m < NPT; ++m) {
       const int c4 = t + V2_CONS * m;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) xv[4 * m + u] = c4 < n4 ? step(4 * c4 + u) : 0.f;
+      for (int u = 0; u < 4; ++u) {
+        float y;
+        xv[4 * m + u] = c4 < n4 ? step(4 * c4 + u, y) : 0.f;
+      }
     }
     // w_j = [mu_j + rho (G y^{k+1} + g)_j]_+ with G y^{k+1} = (1 + beta) r_j - beta (G x^{k-1})_j,
     // r_j = (G x^k)_j: w_j = [A_j + rho (1 + beta) r_j]_+, A_j = mu_j + rho (g_j - beta (G x^{k-1})_j)
     for (int j = j0 + t; j < j1; j += V2_CONS) xs[j - j0] = a.mu[j] + a.rho * (a.g[j] - a.beta_next * a.gx1[j]);
   }
+  if (qcta && a.cpart) {
+    const float v = v2_warp_sum(csum);
+    if (lane == 0) sred[0][warp] = v;  // sred is otherwise used by G-CTAs only
+  }
   v2_consumer_sync();  // xs complete
+  if (qcta && a.cpart && t == 0) {
+    float v = 0.f;
+    for (int w = 0; w < V2_CONS / 32; ++w) v += sred[0][w];
+    a.cpart[c] = v;
+  }
 
   uint32_t gc = 0;
   if (qcta) {
@@ -319,11 +367,31 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
   }
 }
 
+// Step certificate of the last launched iteration, when the loop ran out of
+// iterations before a later launch could read it (one warp).
+__global__ void k_v2_final(const float* cprev, int nQ, float ccoef, int kprev, int* done, int* kstop,
+                           double* cert) {
+  if (*(volatile const int*)done) return;
+  const int lane = threadIdx.x;
+  float v = 0.f;
+  for (int i = lane; i < nQ; i += 32) v += __ldcg(cprev + i);
+  v = v2_warp_sum(v);
+  if (lane == 0) {
+    *cert = (double)(ccoef * v);
+    *kstop = kprev;
+    __threadfence();
+    *(volatile int*)done = 1;
+  }
+}
+
 // Q x^k = row dots + column partials of the Q-CTAs; G' w(y^{k+1}) = column
-// partials of the G-CTAs.  A block owns 32 float4 columns; its 8 thread groups
-// take the partial vectors c = gi, gi + 8, ... (Kahan sums in FP32), and the
-// 8 group sums are added in group order: deterministic for a fixed grid split.
-static constexpr int V2R_COLS = 32, V2R_GROUPS = 8;
+// partials of the G-CTAs.  A block owns 8 float4 columns (128 bytes of every
+// partial vector); its 32 thread groups split the partial vectors: with both
+// sums, groups 0..15 take the Q-CTA vectors c = g, g + 16, ... and groups
+// 16..31 the G-CTA vectors, so both sums load at once (Kahan sums in FP32);
+// the group sums are then added in group order: deterministic for a fixed
+// grid split.
+static constexpr int V2R_COLS = 8, V2R_GROUPS = 32;
 
 __device__ __forceinline__ void v2r_kahan(float4& s, float4& e, const float4 v) {
   v2_kahan(s.x, e.x, v.x);
@@ -340,44 +408,44 @@ __global__ void __launch_bounds__(V2R_COLS* V2R_GROUPS) k_v2_reduce(const float4
   if (done && *(volatile const int*)done) return;
   const int col = threadIdx.x % V2R_COLS, gi = threadIdx.x / V2R_COLS;
   const int c4 = blockIdx.x * V2R_COLS + col;
-  const bool in = c4 < n4;
-  for (int which = 0; which < (tnout ? 2 : 1); ++which) {
-    const int c0 = which == 0 ? 0 : nQ, c1 = which == 0 ? nQ : nQ + nG;
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f), e = s;
-    if (in) {
-      int cc = c0 + gi;
-      for (; cc + 3 * V2R_GROUPS < c1; cc += 4 * V2R_GROUPS) {  // four loads in flight, then the sums in order
-        const float4 v0 = __ldcg(partials + (size_t)cc * n4 + c4);
-        const float4 v1 = __ldcg(partials + (size_t)(cc + V2R_GROUPS) * n4 + c4);
-        const float4 v2 = __ldcg(partials + (size_t)(cc + 2 * V2R_GROUPS) * n4 + c4);
-        const float4 v3 = __ldcg(partials + (size_t)(cc + 3 * V2R_GROUPS) * n4 + c4);
-        v2r_kahan(s, e, v0);
-        v2r_kahan(s, e, v1);
-        v2r_kahan(s, e, v2);
-        v2r_kahan(s, e, v3);
-      }
-      for (; cc < c1; cc += V2R_GROUPS) v2r_kahan(s, e, __ldcg(partials + (size_t)cc * n4 + c4));
+  const int ng = tnout ? V2R_GROUPS / 2 : V2R_GROUPS;  // groups per sum
+  const int which = gi / ng, gl = gi % ng;
+  const int c0 = which == 0 ? 0 : nQ, c1 = which == 0 ? nQ : nQ + nG;
+  float4 s = make_float4(0.f, 0.f, 0.f, 0.f), e = s;
+  if (c4 < n4) {
+    int cc = c0 + gl;
+    for (; cc + 3 * ng < c1; cc += 4 * ng) {  // four loads in flight, then the sums in order
+      const float4 v0 = __ldcg(partials + (size_t)cc * n4 + c4);
+      const float4 v1 = __ldcg(partials + (size_t)(cc + ng) * n4 + c4);
+      const float4 v2 = __ldcg(partials + (size_t)(cc + 2 * ng) * n4 + c4);
+      const float4 v3 = __ldcg(partials + (size_t)(cc + 3 * ng) * n4 + c4);
+      v2r_kahan(s, e, v0);
+      v2r_kahan(s, e, v1);
+      v2r_kahan(s, e, v2);
+      v2r_kahan(s, e, v3);
     }
-    sh[0][gi][col] = s;
-    sh[1][gi][col] = make_float4(-e.x, -e.y, -e.z, -e.w);
-    __syncthreads();
-    if (gi == 0 && in) {
-      double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-      for (int q = 0; q < V2R_GROUPS; ++q) {
-        const float4 h = sh[0][q][col], l = sh[1][q][col];
-        r0 += double(h.x) + double(l.x);
-        r1 += double(h.y) + double(l.y);
-        r2 += double(h.z) + double(l.z);
-        r3 += double(h.w) + double(l.w);
-      }
-      if (which == 0) {
-        const float4 d = ((const float4*)dotQ)[c4];
-        ((float4*)qxout)[c4] = make_float4(float(r0 + d.x), float(r1 + d.y), float(r2 + d.z), float(r3 + d.w));
-      } else {
-        ((float4*)tnout)[c4] = make_float4(float(r0), float(r1), float(r2), float(r3));
-      }
+    for (; cc < c1; cc += ng) v2r_kahan(s, e, __ldcg(partials + (size_t)cc * n4 + c4));
+  }
+  sh[0][gi][col] = s;
+  sh[1][gi][col] = make_float4(-e.x, -e.y, -e.z, -e.w);
+  __syncthreads();
+  const int w = threadIdx.x / V2R_COLS, cw = blockIdx.x * V2R_COLS + threadIdx.x % V2R_COLS;
+  if (w < (tnout ? 2 : 1) && cw < n4) {  // thread (w, col) adds the ng groups of sum w in order
+    const int cl = threadIdx.x % V2R_COLS;
+    double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+    for (int q = w * ng; q < (w + 1) * ng; ++q) {
+      const float4 h = sh[0][q][cl], l = sh[1][q][cl];
+      r0 += double(h.x) + double(l.x);
+      r1 += double(h.y) + double(l.y);
+      r2 += double(h.z) + double(l.z);
+      r3 += double(h.w) + double(l.w);
     }
-    __syncthreads();
+    if (w == 0) {
+      const float4 d = ((const float4*)dotQ)[cw];
+      ((float4*)qxout)[cw] = make_float4(float(r0 + d.x), float(r1 + d.y), float(r2 + d.z), float(r3 + d.w));
+    } else {
+      ((float4*)tnout)[cw] = make_float4(float(r0), float(r1), float(r2), float(r3));
+    }
   }
 }
 

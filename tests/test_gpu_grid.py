@@ -185,3 +185,34 @@ def test_fp32_equality_eps_optimal(ctx, n, p, n_zero):
     x = xl if r.converged_last else xa
     assert O.infeas(qp, x) <= eps * 1.01
     assert O.F(qp, x) - ref.d_lb <= eps * 1.01
+
+
+@pytest.mark.parametrize("alg", ["DFGM", "ADFGM"])
+def test_fp32_step_certificate(ctx, alg, monkeypatch):
+    """Single-pass FP32 inner loops stop on the step certificate (sigma > 0): a first inner
+    solve stops within one iteration of the FP64 oracle stopping on the same certificate,
+    and a full certificate-mode run re-scored in FP64 is eps-optimal, as is the run that
+    stops on the certificate at x^k (DQ_STEP_CERT=0)."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=1028, p=517, seed=41, g_scale=0.05, lam_lo=1.0, lam_hi=30.0)
+    c = exact_constants(inst, alg)
+    P = gpu_problem(ctx, inst, D.FP32)
+    qp = oracle_qp(inst)
+    for eps_in in (1e-3, 1e-5):
+        o = gpu_opts_from(c, alg, eps_in=eps_in, fixed_outer=1, output=D.OUT_AVERAGE, engine=D.ENGINE_GRID)
+        _, _, _, (r,) = P.solve(o)
+        ro = O.dfom(qp, ALG_IDS[alg], c, eps_in=eps_in, outer_fixed=1, want_last=False, inner_cert_step=True)
+        assert abs(r.inner_iters - ro.inner_iters) <= 1, (r.inner_iters, ro.inner_iters)
+    eps = 1e-3
+    ref = O.dfom(qp, ALG_IDS[alg], c, eps_out=1e-7, eps_in=1e-11, outer_check_every=5, max_outer=20000)
+    runs = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("DQ_STEP_CERT", flag)
+        o = gpu_opts_from(c, alg, eps_out=eps, eps_in=1e-5, check_every=5, engine=D.ENGINE_GRID)
+        xl, xa, lam, (r,) = P.solve(o)
+        assert r.status == 0
+        x = xl if r.converged_last else xa
+        assert O.infeas(qp, x) <= eps * 1.01
+        assert O.F(qp, x) - ref.d_lb <= eps * 1.01
+        runs[flag] = r.inner_iters
+    assert runs["1"] <= 1.25 * runs["0"], runs

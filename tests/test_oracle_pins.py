@@ -403,3 +403,53 @@ def test_inner_certificates_bound_suboptimality(rho):
     assert O.inner_cert(qp, rho, xstar, mu, LL, inst.lmin_Q) < 1e-12
     assert O.fw_gap(qp, rho, xstar, mu) < 1e-12
     assert O.inner_cert(qp, rho, xstar, mu, LL, 0.0) == O.fw_gap(qp, rho, xstar, mu)
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.5])
+def test_step_certificate_bounds_suboptimality_of_the_step(rho):
+    """The step certificate of y -> x+ = [y - grad/L]_U bounds L_rho(x+, mu) - d_rho(mu) for
+    step points y inside and outside the box, vanishes at the inner minimiser, and its x+ is
+    the inner iterate the FOM step produces (FOM started at y with GM for one step)."""
+    inst, qp = _small(24, n=9, p=6, g_scale=0.02, box=0.5)
+    mu = np.abs(np.random.default_rng(3).standard_normal(6))
+    LL = inst.lmax_Q + rho * np.linalg.norm(inst.G, 2) ** 2
+    xstar, _, _ = O.fom(qp, rho, mu, LL, inst.lmin_Q, np.zeros(9), fixed=30000)
+    assert O.fw_gap(qp, rho, xstar, mu) < 1e-12   # x* is the minimiser over the box
+    phistar = O.lagrangian(qp, rho, xstar, mu)
+    rng = np.random.default_rng(5)
+    tight = 0
+    for t in range(40):
+        y = xstar + rng.standard_normal(9) * 10.0 ** -rng.uniform(0, 6)
+        if t % 2:
+            y = np.clip(y, -0.5, 0.5)
+        b, xp = O.step_cert(qp, rho, y, mu, LL, inst.lmin_Q)
+        x1, _, _ = O.fom(qp, rho, mu, LL, inst.lmin_Q, y, fixed=1, variant=O.INNER_GM)
+        np.testing.assert_allclose(xp, x1, rtol=0, atol=1e-15)
+        assert np.all(xp >= -0.5) and np.all(xp <= 0.5)
+        sub = O.lagrangian(qp, rho, xp, mu) - phistar
+        assert b >= sub - 1e-13
+        tight += b <= 1e3 * max(sub, 1e-16)
+    assert tight > 0                               # not vacuous: within 1e3 of the true gap somewhere
+    b, xp = O.step_cert(qp, rho, xstar, mu, LL, inst.lmin_Q)
+    assert b < 1e-20 and np.allclose(xp, xstar, atol=1e-12)
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_step_certificate_run_matches_kkt(alg):
+    """DFOM whose inner loops stop on the step certificate reaches the brute-force KKT point."""
+    inst, qp = _small(2, n=5, p=4, g_scale=0.02, box=0.3)
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    r = O.dfom(qp, alg, c, eps_in=1e-12, eps_out=1e-8, max_outer=400000, inner_cert_step=True)
+    assert r.status == 0
+    np.testing.assert_allclose(r.x_last, xs, atol=1e-3)
+    assert abs(r.f_last - fs) <= 1e-7 + 1e-6 * abs(fs)
+    assert r.d_lb <= fs + 1e-10
+    eps = 1e-3
+    r = O.dfom(qp, alg, c, eps_in=O.default_eps_in(alg, eps, c.Ld), eps_out=eps, max_outer=100000,
+               inner_cert_step=True)
+    assert r.status == 0
+    if r.converged_last:
+        assert r.infeas_last <= eps and r.f_last - fs <= eps
+    if r.converged_avg:
+        assert r.infeas_avg <= eps and r.f_avg - fs <= eps
