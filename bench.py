@@ -276,7 +276,9 @@ def run_gpu(args):
                      if st["gemv_launches"] else None,
                      "traffic_unit": "bytes per launch (scaled from a smaller capture)",
                      "peak_kind": kind, "launches_timed": st["gemv_launches"],
-                     "gemv_share_of_step": (st["gemv_ms"] / ms) if ms > 0 else None},
+                     "gemv_share_of_step": (st["gemv_ms"] / ms) if ms > 0 else None,
+                     "reduce": ({"kernel": "k_v2_reduce", "us_per_launch": st["reduce_ms"] / st["reduce_launches"] * 1e3,
+                                 "share_of_step": st["reduce_ms"] / ms} if st.get("reduce_launches") else None)},
         "gpu_launches": st["launches"],
         "clocks": clk,
         "e2e": e2e,

@@ -247,12 +247,15 @@ dq_status dq_serve_stop(dq_context *ctx);
  * bottleneck") with CUDA events on the context's stream; launches that
  * returned early because the inner loop had already stopped are not counted.
  * gemv_bytes counts each matrix element once plus the vectors read and
- * written once (the algorithmic bytes of those launches). */
+ * written once (the algorithmic bytes of those launches).  The single-pass
+ * form also times its per-iteration partial-sum reduction (reduce_*). */
 typedef struct {
-  int64_t launches;       /* all kernels launched by this context            */
-  int64_t gemv_launches;  /* timed inner-iteration GEMV launches             */
-  double gemv_ms;         /* their summed device time                        */
-  double gemv_bytes;      /* their algorithmic bytes                         */
+  int64_t launches;        /* all kernels launched by this context            */
+  int64_t gemv_launches;   /* timed inner-iteration GEMV launches             */
+  double gemv_ms;          /* their summed device time                        */
+  double gemv_bytes;       /* their algorithmic bytes                         */
+  int64_t reduce_launches; /* timed partial-sum reductions (single-pass form) */
+  double reduce_ms;        /* their summed device time                        */
 } dq_stats;
 
 /* enable != 0 turns per-launch event timing of the GEMV on. */

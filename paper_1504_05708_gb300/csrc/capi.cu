@@ -221,9 +221,11 @@ dq_status dq_context_stats(dq_context* ctx, dq_stats* out, int32_t reset) {
   out->gemv_launches = ctx->gemv_launches;
   out->gemv_ms = ctx->gemv_ms;
   out->gemv_bytes = ctx->gemv_bytes;
+  out->reduce_launches = ctx->reduce_launches;
+  out->reduce_ms = ctx->reduce_ms;
   if (reset) {
-    ctx->launches = ctx->gemv_launches = 0;
-    ctx->gemv_ms = ctx->gemv_bytes = 0.0;
+    ctx->launches = ctx->gemv_launches = ctx->reduce_launches = 0;
+    ctx->gemv_ms = ctx->gemv_bytes = ctx->reduce_ms = 0.0;
   }
   return DQ_OK;
 }

@@ -60,6 +60,8 @@ struct dq_context {
   bool profile = false;
   int64_t gemv_launches = 0;
   double gemv_ms = 0.0, gemv_bytes = 0.0;
+  int64_t reduce_launches = 0;
+  double reduce_ms = 0.0;
   // pinned staging and the captured graph of the last persistent launch
   void* pinned = nullptr;
   size_t pinned_bytes = 0;

@@ -553,7 +553,7 @@ struct GridWs {
   int* rows = nullptr;       // qrow (nQ + 1) then grow (nG + 1)
   float* dotQ = nullptr;
   float4* parts = nullptr;
-  float* cbuf = nullptr;          // step-certificate partials, two buffers of num_sms floats
+  float* cbuf = nullptr;          // step-certificate partials, two buffers of kCertStride floats
   int v2_ctas = 0;
   bool v2_ready = false;
   const void* v2_src = nullptr;  // the matrix packed into Qb (Q, or H below)
@@ -741,6 +741,7 @@ struct GridRun {
 
   // ---- single-pass iteration (grid_v2.cuh): setup and launch
   static constexpr double kV2GWeight = 0.8;  // best of a sweep at n = 20000, p = 10000 (0.6 .. 1.25)
+  static constexpr int kCertStride = 256;    // >= reduction blocks for n <= 20480
   bool use_v2 = false;
   int v2_nQ = 0, v2_nG = 0, v2_npt = 0;
   size_t v2_smem = 0;
@@ -757,7 +758,7 @@ struct GridRun {
       W->hoff[nb] = acc;
       auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
       const size_t bQ = a256((size_t)acc * 16), bO = a256((size_t)nb * 8), bR = a256((size_t)(B2 + 2) * 4),
-                   bD = a256((size_t)n * 4), bP = a256((size_t)B2 * n4 * 16), bC = a256((size_t)2 * B2 * 4);
+                   bD = a256((size_t)n * 4), bP = a256((size_t)B2 * n4 * 16), bC = a256((size_t)2 * kCertStride * 4);
       if (cudaMalloc(&W->v2mem, bQ + bO + bR + bD + bP + bC) != cudaSuccess) {
         cudaGetLastError();
         set_error("packed-Q allocation failed");
@@ -874,6 +875,7 @@ struct GridRun {
     struct Rec {
       int k, e0;
       double bytes;
+      int kind;  // 0: GEMV / single pass, 1: partial-sum reduction
     };
     std::vector<Rec> recs;
     int evn = 0;
@@ -888,7 +890,7 @@ struct GridRun {
       cudaEventRecord(W->evpool[evn], st);
       cudaError_t ce = rows<false>(J);
       cudaEventRecord(W->evpool[evn + 1], st);
-      recs.push_back({kk, evn, bytes});
+      recs.push_back({kk, evn, bytes, 0});
       evn += 2;
       return ce;
     };
@@ -919,7 +921,8 @@ struct GridRun {
     // (m only sets how often the host looks at the flag).
     const char* sc_env = getenv("DQ_STEP_CERT");
     const bool step_cert = use_v2 && fixed <= 0 && sigma > 0.0 && !(sc_env && atoi(sc_env) == 0);
-    const int nsm = P->ctx->num_sms;
+    const int ncert = (n / 4 + V2R_COLS - 1) / V2R_COLS;  // blocks of the reduction (<= kCertStride)
+    auto cert_buf = [&](int j) { return W->cbuf + (j & 1) * kCertStride; };
     const float ccoef = (float)(LL * LL * (0.5 / sigma - 0.5 / LL));
     while (k < kmax && kstop < 0) {
       // one chunk of up to m iterations, then (gap mode) the certificate
@@ -931,44 +934,60 @@ struct GridRun {
         if (use_v2) {
           if constexpr (std::is_same<T, float>::value) {
             const double bnext = next_beta();
+            // x^{k+1} = [y - grad/L]_U is formed by the reduction after pass k (and x^1
+            // by k_v2_step); pass k reads x^k
+            V2Step S;
+            memset(&S, 0, sizeof(S));
+            S.addv = aug ? q() : v(W->c); S.lb = lb(); S.ub = ub(); S.L = (float)LL;
+            if (k == 1) {  // y^1 = x^0
+              S.xk = v(X[sx]); S.xkm1 = v(X[sx]); S.qxkm1 = v(QX[sx]); S.b = 0.f; S.xnext = v(X[sn]);
+              S.cpart = step_cert ? cert_buf(1) : nullptr;
+              k_v2_step<<<ncert, 32, 0, st>>>(v(QX[sx]), aug ? v(W->tn) : nullptr, n / 4, S);
+              ++P->ctx->launches;
+              if ((e = cudaGetLastError()) != cudaSuccess) break;
+            }
             V2Args A;
             memset(&A, 0, sizeof(A));
             A.n = n; A.p = p; A.n4 = n / 4; A.nQ = v2_nQ; A.nG = v2_nG;
             A.grow = W->rows; A.boff = W->boff; A.Qb = W->Qb; A.G = G();
-            A.x1 = v(X[sx]); A.x2 = v(X[sxp]); A.qx1 = v(QX[sx]); A.qx2 = v(QX[sxp]);
-            A.tn = aug ? v(W->tn) : nullptr; A.addv = aug ? q() : v(W->c); A.lb = lb(); A.ub = ub();
-            A.gx1 = v(GX[sx]); A.mu = mu; A.g = g();
-            A.beta_prev = (float)beta; A.beta_next = (float)bnext; A.L = (float)LL; A.rho = (float)rho; A.cone = cone;
-            A.xout = v(X[sn]); A.gxout = v(GX[sn]); A.dotQ = W->dotQ; A.partials = W->parts;
+            A.xk = v(X[sn]); A.gx1 = v(GX[sx]); A.mu = mu; A.g = g();
+            A.beta_next = (float)bnext; A.rho = (float)rho; A.cone = cone;
+            A.gxout = v(GX[sn]); A.dotQ = W->dotQ; A.partials = W->parts;
             A.done = fixed > 0 ? nullptr : &W->ctrl->inner_done;
             A.err = &W->ctrl->wait_err;
             if (step_cert) {
-              A.cpart = W->cbuf + (k & 1) * nsm;
-              A.cprev = k > 1 ? W->cbuf + ((k - 1) & 1) * nsm : nullptr;
-              A.ccoef = ccoef; A.eps_in = (float)eps_in; A.kprev = k - 1; A.kmax = kmax;
+              A.cprev = k > 1 ? cert_buf(k - 1) : nullptr;
+              A.ncert = ncert; A.ccoef = ccoef; A.eps_in = (float)eps_in; A.kprev = k - 1; A.kmax = kmax;
               A.kstop = &W->ctrl->k_stop; A.cert = &W->ctrl->cert;
             }
-            const double bytes = 4.0 * (4.0 * double(W->hoff[n / 4]) + (aug ? double(p) * n : 0.0) + 10.0 * n +
+            S.xk = v(X[sn]); S.xkm1 = v(X[sx]); S.qxkm1 = v(QX[sx]); S.b = (float)bnext;
+            S.xnext = v(X[slot_of(k + 1)]);
+            S.cpart = step_cert ? cert_buf(k + 1) : nullptr;
+            const double bytes = 4.0 * (4.0 * double(W->hoff[n / 4]) + (aug ? double(p) * n : 0.0) + double(n) +
                                         (aug ? 4.0 * p : 0));
-            if (P->ctx->profile) {
-              while ((int)W->evpool.size() < evn + 2) {
+            const bool prof = P->ctx->profile;
+            if (prof) {
+              while ((int)W->evpool.size() < evn + 4) {
                 cudaEvent_t ev;
                 if ((e = cudaEventCreate(&ev)) != cudaSuccess) break;
                 W->evpool.push_back(ev);
               }
+              if (e != cudaSuccess) break;
               cudaEventRecord(W->evpool[evn], st);
-              e = v2_pass(A);
-              cudaEventRecord(W->evpool[evn + 1], st);
-              recs.push_back({k, evn, bytes});
-              evn += 2;
-            } else {
-              e = v2_pass(A);
             }
+            e = v2_pass(A);
+            if (prof) cudaEventRecord(W->evpool[evn + 1], st);
             if (e != cudaSuccess) break;
-            k_v2_reduce<<<(n / 4 + V2R_COLS - 1) / V2R_COLS, V2R_COLS * V2R_GROUPS, 0, st>>>(
-                W->parts, v2_nQ, v2_nG, n / 4, W->dotQ, v(QX[sn]), aug ? v(W->tn) : nullptr, dn);
+            k_v2_reduce<<<ncert, V2R_COLS * V2R_GROUPS, 0, st>>>(W->parts, v2_nQ, v2_nG, n / 4, W->dotQ, v(QX[sn]),
+                                                                 aug ? v(W->tn) : nullptr, S, dn);
             ++P->ctx->launches;
             if ((e = cudaGetLastError()) != cudaSuccess) break;
+            if (prof) {
+              cudaEventRecord(W->evpool[evn + 2], st);
+              recs.push_back({k, evn, bytes, 0});
+              recs.push_back({k, evn + 1, 0.0, 1});
+              evn += 3;
+            }
             beta = bnext;
           }
           continue;
@@ -1026,8 +1045,8 @@ struct GridRun {
       }
     }
     if (e == cudaSuccess && step_cert && k > 0) {  // the last iteration's certificate, if no launch read it
-      k_v2_final<<<1, 32, 0, st>>>(W->cbuf + (k & 1) * nsm, v2_nQ, ccoef, k, &W->ctrl->inner_done,
-                                   &W->ctrl->k_stop, &W->ctrl->cert);
+      k_v2_final<<<1, 32, 0, st>>>(cert_buf(k), ncert, ccoef, k, &W->ctrl->inner_done, &W->ctrl->k_stop,
+                                   &W->ctrl->cert);
       ++P->ctx->launches;
       e = cudaGetLastError();
     }
@@ -1053,6 +1072,11 @@ struct GridRun {
       if (r.k > kstop) continue;  // returned at once: the loop had already stopped
       float ms = 0.f;
       DQ_CK(cudaEventElapsedTime(&ms, W->evpool[r.e0], W->evpool[r.e0 + 1]));
+      if (r.kind == 1) {
+        P->ctx->reduce_ms += ms;
+        ++P->ctx->reduce_launches;
+        continue;
+      }
       P->ctx->gemv_ms += ms;
       P->ctx->gemv_bytes += r.bytes;
       ++P->ctx->gemv_launches;

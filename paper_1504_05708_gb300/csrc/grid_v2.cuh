@@ -41,25 +41,21 @@ struct V2Args {
   const long long* boff;              // n/4 block offsets (float4 units)
   const float4* Qb;                   // blocked packed upper triangle
   const float* G;                     // p x n
-  const float *x1, *x2, *qx1, *qx2;   // x^{k-1}, x^{k-2}, Q x^{k-1}, Q x^{k-2}
-  const float* tn;                    // G' w(y^k) (rho > 0) or nullptr
-  const float* addv;                  // q (rho > 0) or c = q + G' mu (rho = 0)
-  const float *lb, *ub;
+  const float* xk;                    // x^k (formed by the previous reduction)
   const float *gx1, *mu, *g;          // G x^{k-1}, mu, g
-  float beta_prev, beta_next, L, rho;
+  float beta_next, rho;
   int cone;
-  float* xout;                        // x^k
   float* gxout;                       // G x^k
   float* dotQ;                        // row dots of the packed rows
   float4* partials;                   // (nQ + nG) x n4 (column-indexed)
   int* done;                          // inner loop finished (set by an earlier launch, or below)
   int* err;                           // set to 1 when a bounded wait gave up
-  // step certificate (sigma > 0): this launch writes cpart[c] = sum over the
-  // x-slice of Q-CTA c of (y_j - x_j)^2; at its start every CTA adds the
-  // previous launch's cprev[0..nQ) in the same order, and stops the loop when
+  // step certificate (sigma > 0) of x^{k-1}: the reduction that formed it
+  // wrote one partial sum of (y_j - x_j)^2 per block, cprev[0..ncert); at its
+  // start every CTA adds them in the same order and stops the loop when
   // ccoef * sum <= eps_in (or kprev >= kmax): CTA 0 records cert and kstop.
-  float* cpart;
   const float* cprev;
+  int ncert;
   float ccoef, eps_in;
   int kprev, kmax;
   int* kstop;
@@ -75,9 +71,11 @@ static constexpr unsigned long long V2_WAIT_NS = 2000000000ull;
 
 __device__ __forceinline__ void v2_consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(V2_CONS) : "memory"); }
 
-// Warp sum (butterfly, every lane gets the total).  Each lane's value is
-// already a compensated partial over its columns; the five pairwise levels
-// add at most 5 roundings.
+// Warp sum (butterfly; every lane gets the same bits).  A lane's value is a
+// short FP32 sum over its own columns (at most 2 NPT products per
+// accumulator, each of them small next to the row's total for the dense
+// workloads), so the rounding is dominated by the five pairwise levels here
+// and the compensated sum over the 16 warps.
 __device__ __forceinline__ float v2_warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -106,7 +104,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
     int stop = a.done ? *(volatile const int*)a.done : 0;
     if (!stop && a.cprev) {
       float v = 0.f;
-      for (int i = lane; i < a.nQ; i += 32) v += __ldcg(a.cprev + i);
+      for (int i = lane; i < a.ncert; i += 32) v += __ldcg(a.cprev + i);
       v = v2_warp_sum(v);  // butterfly: the same bits in every lane and every CTA
       const float ct = a.ccoef * v;
       if (ct <= a.eps_in || a.kprev >= a.kmax) {
@@ -170,76 +168,50 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
     pk = first_chunk(0);
     for (int s = 0; s < V2_STAGES && pr < units; ++s) issue_next();
   }
-  // Release chunk gc (every warp, after its last read of the stage); thread 0
-  // then waits for all 16 releases and refills the stage with the next chunk.
-  auto release = [&](uint32_t gc) {
-    const int s = (int)(gc % V2_STAGES);
+  // Release the chunk in stage rs (phase ph) after every warp's last read of
+  // it; thread 0 then waits for all 16 releases and refills the stage with
+  // the next chunk.
+  auto release = [&](int rs, uint32_t ph) {
     __syncwarp();
-    if (lane == 0) tc::mbar_arrive(&empty[s]);
+    if (lane == 0) tc::mbar_arrive(&empty[rs]);
     if (t == 0 && pr < units) {
-      ok = tc::mbar_wait(&empty[s], (gc / V2_STAGES) & 1, V2_WAIT_NS) && ok;
+      ok = tc::mbar_wait(&empty[rs], ph, V2_WAIT_NS) && ok;
       issue_next();
     }
   };
 
-  // ---------------- prologue: x^k = [y - grad(y)/L]_U for this thread's columns
+  // ---------------- prologue: x^k at this thread's columns (registers)
   float xv[NQS], pv[NQS];  // G-CTA: float4 slot m is xv[4m..4m+3], pv[4m..4m+3]
-  const float b = a.beta_prev;
-  auto step = [&](int j, float& y) {
-    const float x = a.x1[j], xp = a.x2[j], qx = a.qx1[j], qxp = a.qx2[j];
-    y = x + b * (x - xp);
-    const float qy = qx + b * (qx - qxp);
-    const float s = y - (qy + a.addv[j] + (a.tn ? a.tn[j] : 0.f)) / a.L;
-    const float l = a.lb[j], h = a.ub[j];
-    return s < l ? l : (s > h ? h : s);
-  };
-  float csum = 0.f;  // step certificate: sum of (y_j - x_j)^2 over this CTA's x-slice
 #pragma unroll
   for (int m = 0; m < NQS; ++m) pv[m] = 0.f;
   if (qcta) {
-    const int per = (n + nQ - 1) / nQ;  // Q-CTA c stores the c-th slice of x^k
 #pragma unroll
     for (int m = 0; m < NQS; ++m) {
       const int j = t + V2_CONS * m;
-      float o = 0.f;
-      if (j < n) {
-        float y;
-        o = step(j, y);
-        if (j >= c * per && j < (c + 1) * per) {
-          a.xout[j] = o;
-          csum = fmaf(y - o, y - o, csum);
-        }
-        const int blk = j >> 2;
-        if (blk >= c && (blk - c) % nQ == 0) xs[((blk - c) / nQ) * 4 + (j & 3)] = o;
-      }
-      xv[m] = o;
+      xv[m] = j < n ? __ldcg(a.xk + j) : 0.f;
     }
+    for (int i = t; i < 4 * cnt; i += V2_CONS) xs[i] = __ldcg(a.xk + 4 * (c + (i >> 2) * nQ) + (i & 3));
   } else {
 #pragma unroll
     for (int m = 0; m < NPT; ++m) {
       const int c4 = t + V2_CONS * m;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float y;
-        xv[4 * m + u] = c4 < n4 ? step(4 * c4 + u, y) : 0.f;
-      }
+      const float4 x4 = c4 < n4 ? __ldcg((const float4*)a.xk + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      xv[4 * m] = x4.x;
+      xv[4 * m + 1] = x4.y;
+      xv[4 * m + 2] = x4.z;
+      xv[4 * m + 3] = x4.w;
     }
     // w_j = [mu_j + rho (G y^{k+1} + g)_j]_+ with G y^{k+1} = (1 + beta) r_j - beta (G x^{k-1})_j,
     // r_j = (G x^k)_j: w_j = [A_j + rho (1 + beta) r_j]_+, A_j = mu_j + rho (g_j - beta (G x^{k-1})_j)
     for (int j = j0 + t; j < j1; j += V2_CONS) xs[j - j0] = a.mu[j] + a.rho * (a.g[j] - a.beta_next * a.gx1[j]);
   }
-  if (qcta && a.cpart) {
-    const float v = v2_warp_sum(csum);
-    if (lane == 0) sred[0][warp] = v;  // sred is otherwise used by G-CTAs only
-  }
   v2_consumer_sync();  // xs complete
-  if (qcta && a.cpart && t == 0) {
-    float v = 0.f;
-    for (int w = 0; w < V2_CONS / 32; ++w) v += sred[0][w];
-    a.cpart[c] = v;
-  }
 
-  uint32_t gc = 0;
+  // consumer cursor: stage and phase of the next chunk (chunk g sits in stage
+  // g % STAGES with phase (g / STAGES) & 1)
+  int rs = 0;
+  uint32_t rph = 0;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (qcta) {
     for (int rb = 0; rb < cnt; rb += V2_RB) {
       const int re = min(cnt, rb + V2_RB);
@@ -247,32 +219,41 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
         const int blk = c + idx * nQ;
         const int f0 = 4 * blk, kf = f0 / V2_CH4;
         const float4 xq = *(const float4*)(xs + 4 * idx);
+        // four row dots, two FP32 accumulators each (even / odd half of every
+        // chunk): a thread adds at most 2 NPT small products per accumulator
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
 #pragma unroll
         for (int k = 0; k < 2 * NPT; ++k) {
           if (k >= kf && k <= klq) {  // the same for every thread of the CTA
-            const int s = (int)(gc % V2_STAGES);
-            ok = tc::mbar_wait(&full[s], (gc / V2_STAGES) & 1, V2_WAIT_NS) && ok;
-            const float4* ch = ring + (size_t)s * V2_CH4;  // column j at ch[j - k * V2_CH4]
+            ok = tc::mbar_wait(&full[rs], rph, V2_WAIT_NS) && ok;
+            const float4* ch = ring + (size_t)rs * V2_CH4;  // columns k CH4 + t and k CH4 + t + CONS
             const int m0 = 2 * k, ja = t + V2_CONS * m0, jb = ja + V2_CONS;
-            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 va = (ja >= f0 && ja < n) ? ch[ja - k * V2_CH4] : z4;
-            const float4 vb = (jb >= f0 && jb < n) ? ch[jb - k * V2_CH4] : z4;
+            float4 va = ch[t], vb = ch[t + V2_CONS];
+            if (k == kf || k == klq) {  // left of the block's first column, or past n: zero
+              if (ja < f0 || ja >= n) va = z4;
+              if (jb < f0 || jb >= n) vb = z4;
+            }
             const float xa = xv[m0], xb = xv[m0 + 1];
-            // four independent row dots (Kahan per row, both columns folded in one step)
-            v2_kahan(s0, e0, fmaf(va.x, xa, vb.x * xb));
-            v2_kahan(s1, e1, fmaf(va.y, xa, vb.y * xb));
-            v2_kahan(s2, e2, fmaf(va.z, xa, vb.z * xb));
-            v2_kahan(s3, e3, fmaf(va.w, xa, vb.w * xb));
+            s0 = fmaf(va.x, xa, s0);
+            e0 = fmaf(vb.x, xb, e0);
+            s1 = fmaf(va.y, xa, s1);
+            e1 = fmaf(vb.y, xb, e1);
+            s2 = fmaf(va.z, xa, s2);
+            e2 = fmaf(vb.z, xb, e2);
+            s3 = fmaf(va.w, xa, s3);
+            e3 = fmaf(vb.w, xb, e3);
             // column updates x_{4b+r} Q[4b+r, j]
             pv[m0] = fmaf(xq.x, va.x, fmaf(xq.y, va.y, fmaf(xq.z, va.z, fmaf(xq.w, va.w, pv[m0]))));
             pv[m0 + 1] = fmaf(xq.x, vb.x, fmaf(xq.y, vb.y, fmaf(xq.z, vb.z, fmaf(xq.w, vb.w, pv[m0 + 1]))));
-            release(gc);
-            ++gc;
+            release(rs, rph);
+            if (++rs == V2_STAGES) {
+              rs = 0;
+              rph ^= 1u;
+            }
           }
         }
-        const float4 tot = make_float4(v2_warp_sum(s0 - e0), v2_warp_sum(s1 - e1), v2_warp_sum(s2 - e2),
-                                       v2_warp_sum(s3 - e3));
+        const float4 tot = make_float4(v2_warp_sum(s0 + e0), v2_warp_sum(s1 + e1), v2_warp_sum(s2 + e2),
+                                       v2_warp_sum(s3 + e3));
         if (lane == 0) sdot[idx - rb][warp] = tot;
       }
       v2_consumer_sync();
@@ -292,34 +273,39 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
     }
   } else {
     for (int j = j0; j < j1; ++j) {
-      const uint32_t g0 = gc;
-      float sa = 0.f, comp = 0.f;
+      const int rs0 = rs;  // the row's first chunk
+      const uint32_t rph0 = rph;
+      float sa = 0.f, sb = 0.f;
 #pragma unroll
       for (int k = 0; k < NPT / 2; ++k) {
         if (k <= klg) {
-          const uint32_t gk = g0 + k;
-          const int s = (int)(gk % V2_STAGES);
-          ok = tc::mbar_wait(&full[s], (gk / V2_STAGES) & 1, V2_WAIT_NS) && ok;
-          const float4* ch = ring + (size_t)s * V2_CH4;
+          ok = tc::mbar_wait(&full[rs], rph, V2_WAIT_NS) && ok;
+          const float4* ch = ring + (size_t)rs * V2_CH4;  // float4 columns k CH4 + t and k CH4 + t + CONS
           const int m0 = 2 * k, c40 = t + V2_CONS * m0, c41 = c40 + V2_CONS;
-          const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-          const float4 v0 = c40 < n4 ? ch[c40 - k * V2_CH4] : z4;
-          const float4 v1 = c41 < n4 ? ch[c41 - k * V2_CH4] : z4;
-          float d0 = v0.x * xv[4 * m0], d1 = v1.x * xv[4 * m0 + 4];
-          d0 = fmaf(v0.y, xv[4 * m0 + 1], d0);
-          d1 = fmaf(v1.y, xv[4 * m0 + 5], d1);
-          d0 = fmaf(v0.z, xv[4 * m0 + 2], d0);
-          d1 = fmaf(v1.z, xv[4 * m0 + 6], d1);
-          d0 = fmaf(v0.w, xv[4 * m0 + 3], d0);
-          d1 = fmaf(v1.w, xv[4 * m0 + 7], d1);
-          v2_kahan(sa, comp, d0 + d1);
+          float4 v0 = ch[t], v1 = ch[t + V2_CONS];
+          if (k == klg) {
+            if (c40 >= n4) v0 = z4;
+            if (c41 >= n4) v1 = z4;
+          }
+          sa = fmaf(v0.x, xv[4 * m0], sa);
+          sb = fmaf(v1.x, xv[4 * m0 + 4], sb);
+          sa = fmaf(v0.y, xv[4 * m0 + 1], sa);
+          sb = fmaf(v1.y, xv[4 * m0 + 5], sb);
+          sa = fmaf(v0.z, xv[4 * m0 + 2], sa);
+          sb = fmaf(v1.z, xv[4 * m0 + 6], sb);
+          sa = fmaf(v0.w, xv[4 * m0 + 3], sa);
+          sb = fmaf(v1.w, xv[4 * m0 + 7], sb);
+          if (++rs == V2_STAGES) {
+            rs = 0;
+            rph ^= 1u;
+          }
         }
       }
       // one barrier per row: the 16 warp sums go to a buffer that alternates
       // with the row parity (a warp can only write the next row's buffer
       // after every warp has passed this row's barrier), and every warp adds
       // them itself (same order in every warp) to get r_j and w_j
-      const float tot = v2_warp_sum(sa - comp);
+      const float tot = v2_warp_sum(sa + sb);
       float* sr = sred[(j - j0) & 1];
       if (lane == 0) sr[warp] = tot;
       v2_consumer_sync();
@@ -328,26 +314,30 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
       const float wv = xs[j - j0] + a.rho * (1.f + a.beta_next) * rf;
       const float w = a.cone == CONE_EQ ? wv : (wv > 0.f ? wv : 0.f);
       if (t == 0) a.gxout[j] = rf;
+      int us = rs0;
+      uint32_t uph = rph0;
 #pragma unroll
       for (int k = 0; k < NPT / 2; ++k) {
         if (k <= klg) {
-          const int s = (int)((g0 + k) % V2_STAGES);
-          const float4* ch = ring + (size_t)s * V2_CH4;
+          const float4* ch = ring + (size_t)us * V2_CH4;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int m = 2 * k + h, c4 = t + V2_CONS * m;
-            if (c4 < n4) {
-              const float4 gv = ch[c4 - k * V2_CH4];
+            if (k < klg || c4 < n4) {
+              const float4 gv = ch[t + V2_CONS * h];
               pv[4 * m + 0] = fmaf(w, gv.x, pv[4 * m + 0]);
               pv[4 * m + 1] = fmaf(w, gv.y, pv[4 * m + 1]);
               pv[4 * m + 2] = fmaf(w, gv.z, pv[4 * m + 2]);
               pv[4 * m + 3] = fmaf(w, gv.w, pv[4 * m + 3]);
             }
           }
-          release(g0 + k);
+          release(us, uph);
+          if (++us == V2_STAGES) {
+            us = 0;
+            uph ^= 1u;
+          }
         }
       }
-      gc = g0 + klg + 1;
     }
   }
   if (!ok && a.err && lane == 0) atomicExch(a.err, 1);
@@ -384,14 +374,50 @@ __global__ void k_v2_final(const float* cprev, int nQ, float ccoef, int kprev, i
   }
 }
 
+// The next iterate of Algorithm FOM in the x-side form, at four columns:
+//   y = x^k + b (x^k - x^{k-1}),  Q y = Q x^k + b (Q x^k - Q x^{k-1}),
+//   x^{k+1} = [y - (Q y + add + tn) / L]_U,
+// with add = q (rho > 0; tn = G' w(y)) or c = q + G' mu (rho = 0; no tn).
+// Returns the step certificate's sum of (y - x^{k+1})^2 over the four.
+struct V2Step {
+  const float *xk, *xkm1, *qxkm1, *addv, *lb, *ub;
+  float b, L;
+  float* xnext;
+  float* cpart;  // one partial sum per block, or nullptr
+};
+
+__device__ __forceinline__ float v2_step4(const V2Step& st, int c4, const float4 qx, const float4 tn) {
+  const float4 x = __ldcg((const float4*)st.xk + c4), xp = __ldcg((const float4*)st.xkm1 + c4);
+  const float4 qp = __ldcg((const float4*)st.qxkm1 + c4), ad = __ldg((const float4*)st.addv + c4);
+  const float4 lo = __ldg((const float4*)st.lb + c4), hi = __ldg((const float4*)st.ub + c4);
+  const float b = st.b, L = st.L;
+  float sq = 0.f;
+  auto one = [&](float xv, float xpv, float q1, float q0, float a, float t, float l, float h) {
+    const float y = xv + b * (xv - xpv);
+    const float qy = q1 + b * (q1 - q0);
+    const float s = y - (qy + a + t) / L;
+    const float o = s < l ? l : (s > h ? h : s);
+    sq = fmaf(y - o, y - o, sq);
+    return o;
+  };
+  float4 o;
+  o.x = one(x.x, xp.x, qx.x, qp.x, ad.x, tn.x, lo.x, hi.x);
+  o.y = one(x.y, xp.y, qx.y, qp.y, ad.y, tn.y, lo.y, hi.y);
+  o.z = one(x.z, xp.z, qx.z, qp.z, ad.z, tn.z, lo.z, hi.z);
+  o.w = one(x.w, xp.w, qx.w, qp.w, ad.w, tn.w, lo.w, hi.w);
+  ((float4*)st.xnext)[c4] = o;
+  return sq;
+}
+
 // Q x^k = row dots + column partials of the Q-CTAs; G' w(y^{k+1}) = column
-// partials of the G-CTAs.  A block owns 8 float4 columns (128 bytes of every
-// partial vector); its 32 thread groups split the partial vectors: with both
-// sums, groups 0..15 take the Q-CTA vectors c = g, g + 16, ... and groups
-// 16..31 the G-CTA vectors, so both sums load at once (Kahan sums in FP32);
-// the group sums are then added in group order: deterministic for a fixed
-// grid split.
-static constexpr int V2R_COLS = 8, V2R_GROUPS = 32;
+// partials of the G-CTAs; then x^{k+1} from them.  A block owns 32 float4
+// columns; its 16 thread groups split the partial vectors: with both sums,
+// groups 0..7 take the Q-CTA vectors c = g, g + 8, ... and groups 8..15 the
+// G-CTA vectors, so both sums load at once (Kahan sums in FP32); the group
+// sums are then added in group order: deterministic for a fixed grid split.
+// Warp 0 forms x^{k+1} at the block's columns and the block's partial sum of
+// the step certificate.
+static constexpr int V2R_COLS = 32, V2R_GROUPS = 16;
 
 __device__ __forceinline__ void v2r_kahan(float4& s, float4& e, const float4 v) {
   v2_kahan(s.x, e.x, v.x);
@@ -400,11 +426,18 @@ __device__ __forceinline__ void v2r_kahan(float4& s, float4& e, const float4 v) 
   v2_kahan(s.w, e.w, v.w);
 }
 
+__device__ __forceinline__ void v2_cert_store(const V2Step& st, float sq) {
+  const float v = v2_warp_sum(sq);
+  if (st.cpart && threadIdx.x == 0) st.cpart[blockIdx.x] = v;
+}
+
 __global__ void __launch_bounds__(V2R_COLS* V2R_GROUPS) k_v2_reduce(const float4* __restrict__ partials, int nQ,
                                                                      int nG, int n4, const float* __restrict__ dotQ,
                                                                      float* __restrict__ qxout,
-                                                                     float* __restrict__ tnout, const int* done) {
+                                                                     float* __restrict__ tnout, V2Step st,
+                                                                     const int* done) {
   __shared__ float4 sh[2][V2R_GROUPS][V2R_COLS];
+  __shared__ float4 sres[2][V2R_COLS];  // Q x^k, G' w(y^{k+1}) at the block's columns
   if (done && *(volatile const int*)done) return;
   const int col = threadIdx.x % V2R_COLS, gi = threadIdx.x / V2R_COLS;
   const int c4 = blockIdx.x * V2R_COLS + col;
@@ -429,24 +462,48 @@ __global__ void __launch_bounds__(V2R_COLS* V2R_GROUPS) k_v2_reduce(const float4
   sh[0][gi][col] = s;
   sh[1][gi][col] = make_float4(-e.x, -e.y, -e.z, -e.w);
   __syncthreads();
-  const int w = threadIdx.x / V2R_COLS, cw = blockIdx.x * V2R_COLS + threadIdx.x % V2R_COLS;
-  if (w < (tnout ? 2 : 1) && cw < n4) {  // thread (w, col) adds the ng groups of sum w in order
-    const int cl = threadIdx.x % V2R_COLS;
+  const int w = threadIdx.x / V2R_COLS;
+  if (w < 2 && c4 < n4) {  // thread (w, col) adds the ng groups of sum w in order (w = 1: G' w, or zero)
     double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
-    for (int q = w * ng; q < (w + 1) * ng; ++q) {
-      const float4 h = sh[0][q][cl], l = sh[1][q][cl];
-      r0 += double(h.x) + double(l.x);
-      r1 += double(h.y) + double(l.y);
-      r2 += double(h.z) + double(l.z);
-      r3 += double(h.w) + double(l.w);
+    if (w == 0 || tnout) {
+      for (int q = w * ng; q < (w + 1) * ng; ++q) {
+        const float4 h = sh[0][q][col], l = sh[1][q][col];
+        r0 += double(h.x) + double(l.x);
+        r1 += double(h.y) + double(l.y);
+        r2 += double(h.z) + double(l.z);
+        r3 += double(h.w) + double(l.w);
+      }
     }
+    float4 r;
     if (w == 0) {
-      const float4 d = ((const float4*)dotQ)[cw];
-      ((float4*)qxout)[cw] = make_float4(float(r0 + d.x), float(r1 + d.y), float(r2 + d.z), float(r3 + d.w));
+      const float4 d = ((const float4*)dotQ)[c4];
+      r = make_float4(float(r0 + d.x), float(r1 + d.y), float(r2 + d.z), float(r3 + d.w));
+      ((float4*)qxout)[c4] = r;
     } else {
-      ((float4*)tnout)[cw] = make_float4(float(r0), float(r1), float(r2), float(r3));
+      r = make_float4(float(r0), float(r1), float(r2), float(r3));
+      if (tnout) ((float4*)tnout)[c4] = r;
     }
+    sres[w][col] = r;
   }
+  __syncthreads();
+  if (w == 0) {  // warp 0: x^{k+1} and the certificate's partial sum
+    const float sq = c4 < n4 ? v2_step4(st, c4, sres[0][col], sres[1][col]) : 0.f;
+    v2_cert_store(st, sq);
+  }
+}
+
+// x^1 from x^0 (y^1 = x^0): the same step with Q x^0 and G' w(x^0) read from
+// memory; blocks of 32 float4 columns like the reduction, one warp each.
+__global__ void __launch_bounds__(32) k_v2_step(const float* __restrict__ qx, const float* __restrict__ tn, int n4,
+                                               V2Step st) {
+  const int c4 = blockIdx.x * 32 + threadIdx.x;
+  float sq = 0.f;
+  if (c4 < n4) {
+    const float4 q4 = __ldcg((const float4*)qx + c4);
+    const float4 t4 = tn ? __ldcg((const float4*)tn + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    sq = v2_step4(st, c4, q4, t4);
+  }
+  v2_cert_store(st, sq);
 }
 
 // Blocked packed upper triangle: block b holds rows 4b..4b+3 from column 4b

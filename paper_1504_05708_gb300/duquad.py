@@ -69,7 +69,8 @@ class Outputs(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("gemv_launches", ctypes.c_int64), ("gemv_ms", ctypes.c_double),
-                ("gemv_bytes", ctypes.c_double)]
+                ("gemv_bytes", ctypes.c_double), ("reduce_launches", ctypes.c_int64),
+                ("reduce_ms", ctypes.c_double)]
 
 
 SYMBOLS = ("dq_context_create", "dq_context_destroy", "dq_problem_create", "dq_problem_set_vectors",
