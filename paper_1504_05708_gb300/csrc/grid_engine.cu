@@ -798,8 +798,21 @@ struct GridRun {
     v2_npt = std::max(2, ((n4 + V2_CONS - 1) / V2_CONS + 1) / 2 * 2);
     // xs: the four x of each of a Q-CTA's blocks (blocks dealt round-robin), or a G-CTA's row constants
     const size_t xs_len = std::max<size_t>(4 * (size_t)((nb + nQ - 1) / nQ), nG > 0 ? (size_t)(p + nG - 1) / nG : 0) + 4;
+    // the ring (V2_STAGES stages of 16 KB) and xs must fit in shared memory, else
+    // the two-pass form runs (xs grows with p / nG for very wide G)
     v2_smem = (size_t)V2_STAGES * V2_CH4 * 16 + xs_len * 4 + 256;
+    if (v2_smem > max_dynamic_smem(v2_kernel(), P->ctx->smem_optin)) use_v2 = false;
     return DQ_OK;
+  }
+
+  const void* v2_kernel() const {
+    switch (v2_npt) {
+      case 2: return (const void*)k_v2_pass<2>;
+      case 4: return (const void*)k_v2_pass<4>;
+      case 6: return (const void*)k_v2_pass<6>;
+      case 8: return (const void*)k_v2_pass<8>;
+      default: return (const void*)k_v2_pass<10>;
+    }
   }
 
   cudaError_t v2_pass(const V2Args& A) {
@@ -897,7 +910,7 @@ struct GridRun {
     if (use_v2) {
       dq_status s2 = v2_setup(aug);
       if (s2 != DQ_OK) return s2;
-      if (aug && p > 0) {  // G' w(y^1), y^1 = x^0, for the first single-pass iteration
+      if (use_v2 && aug && p > 0) {  // G' w(y^1), y^1 = x^0, for the first single-pass iteration
         RowJob<T> J = job();
         J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->tn);
         J.vmode = VM_W; J.a0 = v(GX[0]); J.a1 = v(GX[0]); J.a2 = mu; J.a3 = g();

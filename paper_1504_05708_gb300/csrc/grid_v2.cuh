@@ -26,8 +26,9 @@
 // slots (Q: column t + 512 m; G: float4 column t + 512 m): the iterate x^k
 // and the column partial sums never leave registers.  Each CTA writes one
 // partial vector; k_v2_reduce adds the partial vectors in a fixed order
-// (deterministic) and the row dots.  HBM bytes per iteration:
-// 4 (n^2/2 + 2n + p n) instead of 4 (n^2 + 2 p n).
+// (deterministic) and the row dots, and forms the next iterate x^{k+1} from
+// them, so a pass reads only x^k besides the matrices.  HBM bytes per
+// iteration: 4 (n^2/2 + 2n + p n) instead of 4 (n^2 + 2 p n).
 #pragma once
 #include "dq_common.cuh"
 #include "tc_common.cuh"
@@ -65,7 +66,9 @@ struct V2Args {
 static constexpr int V2_CONS = 512;                 // threads (16 warps), all consumers
 static constexpr int V2_THREADS = V2_CONS;
 static constexpr int V2_CH4 = 2 * V2_CONS;          // chunk: 1024 x 16 bytes (16 KB)
-static constexpr int V2_STAGES = 12;                // ring depth (192 KB)
+static constexpr int V2_STAGES = 12;                // ring depth (192 KB); a compile-time depth
+                                                    // ran 8 % faster than the same depth passed
+                                                    // at run time
 static constexpr int V2_RB = 16;                    // Q blocks (64 rows) between flushes of the row dots
 static constexpr unsigned long long V2_WAIT_NS = 2000000000ull;
 
@@ -92,7 +95,7 @@ __device__ __forceinline__ void v2_kahan(float& s, float& c, float v) {
 // block spans at most 2 NPT chunks (4 NPT scalar column slots per thread).
 template <int NPT>
 __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
-  static_assert(NPT % 2 == 0 && NPT / 2 <= V2_STAGES, "chunk ring too shallow");
+  static_assert(NPT % 2 == 0 && NPT / 2 < V2_STAGES, "chunk ring too shallow");
   constexpr int NQS = 4 * NPT;  // scalar column slots of a Q-CTA thread
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(8) uint64_t full[V2_STAGES], empty[V2_STAGES];
@@ -129,9 +132,10 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
   const int j0 = qcta ? 0 : a.grow[c - nQ], j1 = qcta ? 0 : a.grow[c - nQ + 1];
   float4* ring = (float4*)sm;
   // Q-CTA: the four x of each of its blocks; G-CTA: per-row constant of w
-  float* xs = (float*)(sm + (size_t)V2_STAGES * V2_CH4 * 16);
+  constexpr int nst = V2_STAGES;
+  float* xs = (float*)(sm + (size_t)nst * V2_CH4 * 16);
   if (t == 0) {
-    for (int s = 0; s < V2_STAGES; ++s) {
+    for (int s = 0; s < nst; ++s) {
       tc::mbar_init(&full[s], 1);
       tc::mbar_init(&empty[s], V2_CONS / 32);
     }
@@ -139,34 +143,37 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
   }
   __syncthreads();
 
-  // Issue cursor (used by thread 0 only): chunk pk of this CTA's pr-th block
-  // (Q) or row (G); chunk number pg goes to stage pg % STAGES.
+  // Issue cursor (thread 0 only): chunk pk of this CTA's pr-th unit (Q block
+  // or G row), whose data starts at u_src (column / float4 column u_f0).
+  // Stages are refilled in the order they are released, so the chunk issued
+  // after releasing stage s goes to stage s: no stage arithmetic here.
   const int units = qcta ? cnt : j1 - j0;
-  int pr = 0, pk = 0;
-  uint32_t pg = 0;
+  const int lim = qcta ? n : n4, klast = qcta ? klq : klg;
+  int pr = 0, pk = 0, u_f0 = 0;
+  const float4* u_src = nullptr;
   bool ok = true;
-  auto first_chunk = [&](int r) { return qcta ? (4 * (c + r * nQ)) / V2_CH4 : 0; };
-  auto issue_next = [&]() {  // thread 0: copy the cursor's chunk into stage pg % STAGES, advance
-    const int f0 = qcta ? 4 * (c + pr * nQ) : 0;          // first column (Q) / float4 column (G)
-    const int lim = qcta ? n : n4;
-    const int b0 = max(pk * V2_CH4, f0), e0 = min((pk + 1) * V2_CH4, lim);
-    // block offset in closed form: sum_{b' < b} (n - 4 b') = b n - 2 b (b - 1) (no load on the refill path)
-    const long long blk = c + pr * nQ;
-    const float4* src = qcta ? a.Qb + (blk * n - 2 * blk * (blk - 1)) + (b0 - f0)
-                             : (const float4*)(a.G + (size_t)(j0 + pr) * n) + b0;
-    const uint32_t bytes = (uint32_t)(e0 - b0) * 16u;
-    const int s = (int)(pg % V2_STAGES);
-    tc::mbar_expect_tx(&full[s], bytes);
-    tc::bulk_g2s(ring + (size_t)s * V2_CH4 + (b0 - pk * V2_CH4), src, bytes, &full[s]);
-    ++pg;
-    if (++pk > (qcta ? klq : klg)) {
-      ++pr;
-      if (pr < units) pk = first_chunk(pr);
+  auto unit_begin = [&]() {
+    if (qcta) {  // block offset in closed form: sum_{b' < b} (n - 4 b') = b n - 2 b (b - 1)
+      const long long blk = c + (long long)pr * nQ;
+      u_f0 = 4 * (int)blk;
+      u_src = a.Qb + (blk * n - 2 * blk * (blk - 1));
+      pk = u_f0 / V2_CH4;
+    } else {
+      u_f0 = 0;
+      u_src = (const float4*)(a.G + (size_t)(j0 + pr) * n);
+      pk = 0;
     }
   };
+  auto issue_next = [&](int s) {  // copy the cursor's chunk into stage s, advance
+    const int b0 = max(pk * V2_CH4, u_f0), e0 = min((pk + 1) * V2_CH4, lim);
+    const uint32_t bytes = (uint32_t)(e0 - b0) * 16u;
+    tc::mbar_expect_tx(&full[s], bytes);
+    tc::bulk_g2s(ring + (size_t)s * V2_CH4 + (b0 - pk * V2_CH4), u_src + (b0 - u_f0), bytes, &full[s]);
+    if (++pk > klast && ++pr < units) unit_begin();
+  };
   if (t == 0 && units > 0) {
-    pk = first_chunk(0);
-    for (int s = 0; s < V2_STAGES && pr < units; ++s) issue_next();
+    unit_begin();
+    for (int s = 0; s < nst && pr < units; ++s) issue_next(s);
   }
   // Release the chunk in stage rs (phase ph) after every warp's last read of
   // it; thread 0 then waits for all 16 releases and refills the stage with
@@ -176,7 +183,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
     if (lane == 0) tc::mbar_arrive(&empty[rs]);
     if (t == 0 && pr < units) {
       ok = tc::mbar_wait(&empty[rs], ph, V2_WAIT_NS) && ok;
-      issue_next();
+      issue_next(rs);
     }
   };
 
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
             pv[m0] = fmaf(xq.x, va.x, fmaf(xq.y, va.y, fmaf(xq.z, va.z, fmaf(xq.w, va.w, pv[m0]))));
             pv[m0 + 1] = fmaf(xq.x, vb.x, fmaf(xq.y, vb.y, fmaf(xq.z, vb.z, fmaf(xq.w, vb.w, pv[m0 + 1]))));
             release(rs, rph);
-            if (++rs == V2_STAGES) {
+            if (++rs == nst) {
               rs = 0;
               rph ^= 1u;
             }
@@ -295,7 +302,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
           sb = fmaf(v1.z, xv[4 * m0 + 6], sb);
           sa = fmaf(v0.w, xv[4 * m0 + 3], sa);
           sb = fmaf(v1.w, xv[4 * m0 + 7], sb);
-          if (++rs == V2_STAGES) {
+          if (++rs == nst) {
             rs = 0;
             rph ^= 1u;
           }
@@ -332,7 +339,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
             }
           }
           release(us, uph);
-          if (++us == V2_STAGES) {
+          if (++us == nst) {
             us = 0;
             uph ^= 1u;
           }
@@ -415,6 +422,8 @@ __device__ __forceinline__ float v2_step4(const V2Step& st, int c4, const float4
 // groups 0..7 take the Q-CTA vectors c = g, g + 8, ... and groups 8..15 the
 // G-CTA vectors, so both sums load at once (Kahan sums in FP32); the group
 // sums are then added in group order: deterministic for a fixed grid split.
+// (1024-thread blocks with eight loads in flight ran at half the speed: one
+// block per SM and a second wave.)
 // Warp 0 forms x^{k+1} at the block's columns and the block's partial sum of
 // the step certificate.
 static constexpr int V2R_COLS = 32, V2R_GROUPS = 16;
