@@ -758,7 +758,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-inner-sample", type=int, default=8)
-    ap.add_argument("--ref-inner-per-solve", type=int, default=5430)
+    ap.add_argument("--ref-inner-per-solve", type=int, default=5246)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

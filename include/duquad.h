@@ -50,9 +50,24 @@ typedef enum { DQ_OUT_LAST = 1, DQ_OUT_AVERAGE = 2, DQ_OUT_BOTH = 3 } dq_output;
 typedef enum { DQ_FP64 = 0, DQ_FP32 = 1, DQ_BF16X3 = 2 } dq_precision;
 
 /* Inner stopping rule: DQ_INNER_GAP stops the inner loop of Algorithm FOM when
- * the Frank-Wolfe gap of L_rho(., mu) over the box is <= eps_in (a certificate
- * of eq. duquad_in); DQ_INNER_FIXED runs exactly fixed_inner iterations. */
+ * a certificate of eq. duquad_in (an upper bound on L_rho(x, mu) - d_rho(mu))
+ * is <= eps_in; DQ_INNER_FIXED runs exactly fixed_inner iterations. */
 typedef enum { DQ_INNER_GAP = 0, DQ_INNER_FIXED = 1 } dq_inner_stop;
+
+/* Certificate of DQ_INNER_GAP.  DQ_CERT_POINT: at the iterate x^k, the
+ * gradient-mapping bound <grad, x - x+> + ||L (x - x+)||^2 (1/(2 sigma) -
+ * 1/(2 L)) when sigma > 0, else the Frank-Wolfe gap; it needs the gradient at
+ * x^k (one more G' product when rho > 0).  DQ_CERT_STEP: when sigma > 0, the
+ * bound ||L (y - x^k)||^2 (1/(2 sigma) - 1/(2 L)) of the step y^k -> x^k that
+ * the iteration makes anyway (no extra product); where sigma = 0, or in the
+ * two-pass grid form and the tensor-core batch, the point certificate is used.
+ * DQ_CERT_AUTO (0, the default): the step certificate in the single-pass grid
+ * engine, the point certificate in the thread-block engine.  (The gradient at
+ * y comes from Q y = Q x^k + beta (Q x^k - Q x^{k-1}), which carries about
+ * (1 + 2 beta) times the rounding of one product; the step certificate
+ * squares it, and on FP32 instances with kappa(Q) ~ 1e4 that floor stayed
+ * above eps_in.) */
+typedef enum { DQ_CERT_AUTO = 0, DQ_CERT_POINT = 1, DQ_CERT_STEP = 2 } dq_inner_cert;
 
 typedef enum { DQ_CONE_INEQ = 0, DQ_CONE_EQ = 1 } dq_cone;
 typedef enum { DQ_HOST = 0, DQ_DEVICE = 1 } dq_memory;
@@ -105,7 +120,7 @@ typedef struct {
   int32_t inner_stop;      /* dq_inner_stop                                    */
   int32_t engine;          /* dq_engine                                        */
   double eps_out;          /* outer certificate tolerance (default 1e-3)       */
-  double eps_in;           /* inner FW-gap tolerance (default: eq. choose_ein,
+  double eps_in;           /* inner certificate tolerance (default: eq. choose_ein,
                               eps_out/4 for (A)DGM, eps_out^1.5/(8 sqrt(2 L_d))
                               for (A)DFGM with R_d = 1)                       */
   double rho;              /* NaN: 0 for DGM/DFGM, 1/||G||^2 for ADGM/ADFGM    */
@@ -121,6 +136,7 @@ typedef struct {
   int32_t fresh_constants; /* 1: recompute lambda_max(Q) and ||G||^2 in this
                               solve instead of reusing the handle's (given
                               values in dq_problem_desc are always kept)       */
+  int32_t inner_cert;      /* dq_inner_cert (default DQ_CERT_AUTO)             */
 } dq_solve_opts;
 
 /* Result of one solve (one instance). */

@@ -187,6 +187,11 @@ dq_status resolve_opts(const dq_problem* P, const dq_solve_opts* o, SolveCfg* c)
   c->Ld = o->Ld;
   c->LL = o->LL;
   c->sigma = o->sigma;
+  if (o->inner_cert < DQ_CERT_AUTO || o->inner_cert > DQ_CERT_STEP) {
+    set_error("inner_cert must be DQ_CERT_AUTO, DQ_CERT_POINT or DQ_CERT_STEP");
+    return DQ_ERR_INVALID;
+  }
+  c->inner_cert = o->inner_cert;
   (void)P;
   return DQ_OK;
 }

@@ -41,6 +41,7 @@ struct SolveCfg {
   double eps_out, eps_in, rho;
   int fixed_outer, fixed_inner, max_outer, max_inner, check_every, inner_check_every;
   int warm_start, kd_literal, fresh;
+  int inner_cert;  // dq_inner_cert
   double Ld, LL, sigma;
 };
 

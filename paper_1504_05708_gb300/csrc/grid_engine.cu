@@ -932,8 +932,7 @@ struct GridRun {
     // iterate it makes from its own step, and the next launch stops the loop;
     // the certificate costs no gradient at x^k and is checked every iteration
     // (m only sets how often the host looks at the flag).
-    const char* sc_env = getenv("DQ_STEP_CERT");
-    const bool step_cert = use_v2 && fixed <= 0 && sigma > 0.0 && !(sc_env && atoi(sc_env) == 0);
+    const bool step_cert = use_v2 && fixed <= 0 && sigma > 0.0 && cfg->inner_cert != DQ_CERT_POINT;
     const int ncert = (n / 4 + V2R_COLS - 1) / V2R_COLS;  // blocks of the reduction (<= kCertStride)
     auto cert_buf = [&](int j) { return W->cbuf + (j & 1) * kCertStride; };
     const float ccoef = (float)(LL * LL * (0.5 / sigma - 0.5 / LL));

@@ -402,9 +402,12 @@ __device__ __forceinline__ float v2_step4(const V2Step& st, int c4, const float4
   auto one = [&](float xv, float xpv, float q1, float q0, float a, float t, float l, float h) {
     const float y = xv + b * (xv - xpv);
     const float qy = q1 + b * (q1 - q0);
-    const float s = y - (qy + a + t) / L;
+    const float st = (qy + a + t) / L, s = y - st;
     const float o = s < l ? l : (s > h ? h : s);
-    sq = fmaf(y - o, y - o, sq);
+    // y - x^{k+1} is the step itself where the box is inactive (no cancellation
+    // error of ulp(y), which L^2 / (2 sigma) would turn into a floor of the bound)
+    const float d = (s > l && s < h) ? st : y - o;
+    sq = fmaf(d, d, sq);
     return o;
   };
   float4 o;

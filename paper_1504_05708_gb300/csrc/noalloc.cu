@@ -123,6 +123,7 @@ static dq_status run_noalloc(int device, const dq_problem_desc* d, const SolveCf
   I.Ld = c.Ld;
   I.inner_fixed = c.fixed_inner;
   I.inner_check_every = c.inner_check_every;
+  I.cert_step = c.inner_cert == DQ_CERT_STEP;  // DQ_CERT_AUTO: the point certificate here
   I.max_inner = c.max_inner;
   I.eps_in = c.eps_in;
   I.outer_fixed = c.fixed_outer;

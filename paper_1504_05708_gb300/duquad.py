@@ -21,6 +21,7 @@ ALGS = {"DGM": DGM, "DFGM": DFGM, "ADGM": ADGM, "ADFGM": ADFGM}
 OUT_LAST, OUT_AVERAGE, OUT_BOTH = 1, 2, 3
 FP64, FP32, BF16X3 = 0, 1, 2
 INNER_GAP, INNER_FIXED = 0, 1
+CERT_AUTO, CERT_POINT, CERT_STEP = 0, 1, 2
 CONE_INEQ, CONE_EQ = 0, 1
 HOST, DEVICE = 0, 1
 ENGINE_AUTO, ENGINE_CTA, ENGINE_GRID, ENGINE_TC = 0, 1, 2, 3
@@ -46,7 +47,7 @@ class SolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("inner_check_every", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("kd_literal", ctypes.c_int32),
                 ("Ld", ctypes.c_double), ("LL", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("fresh_constants", ctypes.c_int32)]
+                ("fresh_constants", ctypes.c_int32), ("inner_cert", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):
@@ -149,7 +150,7 @@ def _ptr(a):
 def opts(alg="DFGM", *, output=OUT_BOTH, inner_stop=INNER_GAP, engine=ENGINE_AUTO, eps_out=1e-3,
          eps_in=NAN, rho=NAN, fixed_outer=0, fixed_inner=0, max_outer=0, max_inner=0, check_every=0,
          inner_check_every=0, warm_start=0, kd_literal=0, Ld=NAN, LL=NAN, sigma=NAN,
-         fresh_constants=0) -> SolveOpts:
+         fresh_constants=0, inner_cert=CERT_AUTO) -> SolveOpts:
     o = SolveOpts()
     o.alg = ALGS[alg] if isinstance(alg, str) else int(alg)
     o.output, o.inner_stop, o.engine = output, inner_stop, engine
@@ -158,6 +159,7 @@ def opts(alg="DFGM", *, output=OUT_BOTH, inner_stop=INNER_GAP, engine=ENGINE_AUT
     o.check_every, o.inner_check_every, o.warm_start, o.kd_literal = check_every, inner_check_every, warm_start, kd_literal
     o.Ld, o.LL, o.sigma = Ld, LL, sigma
     o.fresh_constants = fresh_constants
+    o.inner_cert = inner_cert
     if fixed_inner and inner_stop == INNER_GAP:
         o.inner_stop = INNER_FIXED
     return o

@@ -48,17 +48,21 @@ def test_fp64_fixed_counts_parity(ctx, alg, g_scale):
     assert abs(r.f_last - ro.f_last) <= 1e-9 * max(1, abs(ro.f_last))
 
 
+@pytest.mark.parametrize("cert", ["step", "point"])
 @pytest.mark.parametrize("alg", ALGS)
-def test_fp64_certificate_mode_parity(ctx, alg):
-    """Certificate stopping (inner and outer): same iteration counts and the same iterate."""
+def test_fp64_certificate_mode_parity(ctx, alg, cert):
+    """Certificate stopping (inner and outer): same iteration counts and the same iterate, with
+    the inner loop stopping on the step certificate (the default) or on the one at x^k."""
     from paper_1504_05708_gb300 import duquad as D
     inst = _c0(0.02)
     c = exact_constants(inst, alg)
     eps_in = O.default_eps_in(ALG_IDS[alg], 1e-4, c.Ld)
-    ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, eps_in=eps_in, eps_out=1e-4, max_outer=20000)
+    ro = O.dfom(oracle_qp(inst), ALG_IDS[alg], c, eps_in=eps_in, eps_out=1e-4, max_outer=20000,
+                inner_cert_step=cert == "step")
     P = gpu_problem(ctx, inst, D.FP64)
     xl, xa, lam, (r,) = P.solve(gpu_opts_from(c, alg, eps_in=eps_in, eps_out=1e-4, max_outer=20000,
-                                                engine=D.ENGINE_CTA))
+                                                engine=D.ENGINE_CTA,
+                                                inner_cert=D.CERT_STEP if cert == "step" else D.CERT_POINT))
     assert r.status == ro.status == 0
     assert (r.outer_iters, r.inner_iters) == (ro.outer_iters, ro.inner_iters)
     assert rel(xl, ro.x_last) <= TOL64 and rel(xa, ro.x_avg) <= TOL64
@@ -174,9 +178,37 @@ def test_invalid_inputs_rejected(ctx):
         P.solve(D.opts("DGM", rho=0.5))
     with pytest.raises(D.DuquadError):
         P.solve(D.opts("DFGM", inner_stop=D.INNER_FIXED, fixed_inner=0))
+    with pytest.raises(D.DuquadError) as e:
+        P.solve(D.opts("DFGM", inner_cert=7))
+    assert e.value.status == D.ERR_INVALID
     # DGM needs lambda_min(Q) > 0 (Case 1): a zero lower bound is refused on the device
     Z = gpu_problem(ctx, inst, D.FP64)
     Z2 = D.Problem(ctx, inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, prec=D.FP64, lmin_Q=0.0)
     with pytest.raises(D.DuquadError) as e:
         Z2.solve(D.opts("DGM", engine=D.ENGINE_CTA))
     assert e.value.status == D.ERR_INVALID
+
+
+@pytest.mark.parametrize("alg", ["DFGM", "ADFGM"])
+def test_fp32_default_certificate_ill_conditioned(ctx, alg):
+    """FP32, kappa(Q) = 1e4: the thread-block engine's default inner certificate is the one at
+    x^k (the step certificate squares the rounding of the extrapolated product Q y, which
+    stays above eps_in on such instances): DQ_CERT_AUTO runs exactly as DQ_CERT_POINT, and the
+    result is eps-optimal when re-scored in FP64 against the oracle's lower bound."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=128, p=64, seed=5, g_scale=0.01, g_offset=0.0, kappa=1e4)
+    qp = oracle_qp(inst)
+    c = exact_constants(inst, alg)
+    ref = O.dfom(qp, ALG_IDS[alg], c, eps_out=1e-4, eps_in=1e-8, max_outer=20000)  # d_lb <= F*
+    P = gpu_problem(ctx, inst, D.FP32)
+    eps = 1e-3
+    out = {}
+    for cert in (D.CERT_AUTO, D.CERT_POINT):
+        xl, xa, lam, (r,) = P.solve(D.opts(alg, eps_out=eps, max_outer=5000, engine=D.ENGINE_CTA, inner_cert=cert))
+        assert r.status == 0
+        x = xl if r.converged_last else xa
+        assert O.infeas(qp, x) <= eps * 1.01
+        assert O.F(qp, x) - ref.d_lb <= eps * 1.01
+        out[cert] = (r.outer_iters, r.inner_iters, x)
+    assert out[D.CERT_AUTO][:2] == out[D.CERT_POINT][:2]
+    assert np.array_equal(out[D.CERT_AUTO][2], out[D.CERT_POINT][2])

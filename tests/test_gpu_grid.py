@@ -188,11 +188,11 @@ def test_fp32_equality_eps_optimal(ctx, n, p, n_zero):
 
 
 @pytest.mark.parametrize("alg", ["DFGM", "ADFGM"])
-def test_fp32_step_certificate(ctx, alg, monkeypatch):
+def test_fp32_step_certificate(ctx, alg):
     """Single-pass FP32 inner loops stop on the step certificate (sigma > 0): a first inner
     solve stops within one iteration of the FP64 oracle stopping on the same certificate,
     and a full certificate-mode run re-scored in FP64 is eps-optimal, as is the run that
-    stops on the certificate at x^k (DQ_STEP_CERT=0)."""
+    stops on the certificate at x^k (DQ_CERT_POINT)."""
     from paper_1504_05708_gb300 import duquad as D
     inst = W.single_dense(n=256, p=128, seed=41, g_scale=0.05, lam_lo=1.0, lam_hi=30.0)
     c = exact_constants(inst, alg)
@@ -206,13 +206,12 @@ def test_fp32_step_certificate(ctx, alg, monkeypatch):
     eps = 1e-3
     ref = O.dfom(qp, ALG_IDS[alg], c, eps_out=1e-6, eps_in=1e-10, outer_check_every=5, max_outer=20000)
     runs = {}
-    for flag in ("1", "0"):
-        monkeypatch.setenv("DQ_STEP_CERT", flag)
-        o = gpu_opts_from(c, alg, eps_out=eps, eps_in=1e-5, check_every=5, engine=D.ENGINE_GRID)
+    for cert in (D.CERT_STEP, D.CERT_POINT):
+        o = gpu_opts_from(c, alg, eps_out=eps, eps_in=1e-5, check_every=5, engine=D.ENGINE_GRID, inner_cert=cert)
         xl, xa, lam, (r,) = P.solve(o)
         assert r.status == 0
         x = xl if r.converged_last else xa
         assert O.infeas(qp, x) <= eps * 1.01
         assert O.F(qp, x) - ref.d_lb <= eps * 1.01
-        runs[flag] = r.inner_iters
-    assert runs["1"] <= 1.25 * runs["0"], runs
+        runs[cert] = r.inner_iters
+    assert runs[D.CERT_STEP] <= 1.25 * runs[D.CERT_POINT], runs
