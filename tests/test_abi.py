@@ -51,3 +51,29 @@ def test_oracle_and_product_share_no_code():
         if f.endswith((".py", ".c")):
             src = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_1504_05708_gb300" not in src and "duquad.h" not in src, f
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding marshals has the header's size and field offsets (gcc on the
+    header, no GPU): a field added on one side only would shift every later field."""
+    import subprocess
+    from paper_1504_05708_gb300 import duquad as D
+    pairs = {"dq_problem_desc": D.ProblemDesc, "dq_solve_opts": D.SolveOpts, "dq_result": D.Result,
+             "dq_outputs": D.Outputs, "dq_stats": D.Stats}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "duquad.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            cfield = "lambda" if fname == "lambda_" else fname
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {cfield}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
