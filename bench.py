@@ -133,6 +133,13 @@ class LargeDense:
 
     name = "large_dense_n20000_p10000_fp32_adfgm"
 
+    @staticmethod
+    def workload_name(n, p, alg, equality=False):
+        """The workload as named in the JSON line, with its actual sizes."""
+        if equality:
+            return f"large_dense_eq_n{n}_p{p}_fp32_{alg.lower()}_hessian"
+        return f"large_dense_n{n}_p{p}_fp32_{alg.lower()}"
+
     def __init__(self, args, device, equality=False):
         import torch
 
@@ -142,8 +149,7 @@ class LargeDense:
         self.eps = args.eps
         self.dev = device
         self.equality = equality
-        if equality:
-            self.name = "large_dense_eq_n20000_p10000_fp32_adfgm_hessian"
+        self.name = self.workload_name(self.n, self.p, self.alg, equality)
         d = W.large_dense(n=self.n, p=self.p, seed=1, device=f"cuda:{device}", equality=equality)
         self.d = d
         self.lmin = d["lmin_Q"]
@@ -349,7 +355,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * inner_per_solve * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": LargeDense.name, "n": args.n, "p": args.p, "alg": args.alg, "eps": args.eps},
+            "config": {"workload": LargeDense.workload_name(args.n, args.p, args.alg), "n": args.n, "p": args.p,
+                       "alg": args.alg, "eps": args.eps},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
