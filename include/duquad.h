@@ -279,6 +279,43 @@ dq_status dq_context_profile(dq_context *ctx, int32_t enable);
 /* Copy the counters; reset != 0 zeroes them afterwards. */
 dq_status dq_context_stats(dq_context *ctx, dq_stats *out, int32_t reset);
 
+/* ---- theory mode ----------------------------------------------------------
+ * Iteration counts that the paper's analysis prescribes for a target
+ * accuracy eps (host arithmetic only; needs no GPU).  With R_d an estimate of
+ * the distance from lambda^0 to the optimal multipliers and D_U the box
+ * diameter ||ub - lb||_2:
+ *   rho     given, or (NaN) rho* = 8 R_d^2 / eps for ADGM/ADFGM (the optimal
+ *           smoothing of Sec. 5) and 0 for DGM/DFGM;
+ *   L_L = lmax_Q + rho normG2,  sigma_L = lmin_Q,
+ *   L_d = normG2 / (lmin_Q + rho normG2)                         (eq. Ld);
+ *   eps_in, k_out                                        (eq. choose_ein):
+ *     DGM/ADGM   eps / 4,                        8 L_d R_d^2 / eps
+ *     DFGM/ADFGM eps^{3/2} / (8 R_d sqrt(2 L_d)),  sqrt(8 L_d R_d^2 / eps);
+ *   k_in, Algorithm FOM's count for eps_in (Sec. 5):
+ *     sigma_L = 0: sqrt(2 L_L D_U^2 / eps_in),
+ *     sigma_L > 0: sqrt(L_L / sigma_L) log(L_L D_U^2 / eps_in) + 1;
+ * k_out and k_in are rounded up (at least 1).  A solve with inner_stop =
+ * DQ_INNER_FIXED, fixed_inner = k_in, fixed_outer = k_out, rho = rho and
+ * eps_in = eps_in runs the method exactly as analysed.  DQ_ERR_INVALID: eps,
+ * R_d or D_U not positive and finite, lmax_Q or normG2 not finite, lmin_Q
+ * negative, rho negative, or L_d undefined (DGM/DFGM with lmin_Q = 0). */
+typedef struct {
+  int32_t alg;                    /* dq_algorithm                              */
+  double eps;                     /* target accuracy (> 0)                     */
+  double Rd;                      /* estimate of R_d (> 0)                     */
+  double D_U;                     /* box diameter (> 0)                        */
+  double lmax_Q, lmin_Q, normG2;  /* spectrum constants                        */
+  double rho;                     /* NaN: the default above                    */
+} dq_theory_in;
+
+typedef struct {
+  double rho, LL, sigma, Ld;      /* the constants the counts use              */
+  double eps_in;                  /* inner accuracy (eq. choose_ein)           */
+  int64_t k_out, k_in, k_total;   /* outer, inner per outer, their product     */
+} dq_theory_out;
+
+dq_status dq_theory(const dq_theory_in *in, dq_theory_out *out);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *dq_last_error(void);
 

@@ -317,4 +317,18 @@ def k_out(alg: int, eps: float, Ld: float, Rd: float) -> float:
     return v if alg in (DGM, ADGM) else math.sqrt(v)
 
 
+def k_in(LL: float, sigma: float, D_U: float, eps_in: float) -> float:
+    """Inner iteration count of Algorithm FOM for accuracy eps_in (Sec. 5, proof of the
+    total-complexity theorem, from Lemma sublin_dfg with R_L = D_U):
+    sqrt(2 L D_U^2 / eps_in) for sigma = 0, sqrt(L / sigma) log(L D_U^2 / eps_in) + 1 for sigma > 0."""
+    if sigma > 0.0:
+        return math.sqrt(LL / sigma) * math.log(LL * D_U * D_U / eps_in) + 1.0
+    return math.sqrt(2.0 * LL * D_U * D_U / eps_in)
+
+
+def rho_star(eps: float, Rd: float) -> float:
+    """The smoothing that minimises k_out k_in (Sec. 5): rho* = 8 R_d^2 / eps."""
+    return 8.0 * Rd * Rd / eps
+
+
 from .sampled import sampled_fom_step  # noqa: E402,F401

@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/duquad.h: contexts, the device problem
 // store, option resolution and dispatch to the engines.
 #include <math.h>
+#include <cmath>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -207,6 +208,48 @@ extern "C" {
 const char* dq_last_error(void) { return g_err; }
 
 const char* dq_version(void) { return "duquad-gb300 0.1 (sm_103a)"; }
+
+dq_status dq_theory(const dq_theory_in* in, dq_theory_out* out) {
+  if (!in || !out) {
+    set_error("NULL argument");
+    return DQ_ERR_INVALID;
+  }
+  const bool fast = in->alg == DQ_DFGM || in->alg == DQ_ADFGM, aug = in->alg == DQ_ADGM || in->alg == DQ_ADFGM;
+  auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
+  if (in->alg < DQ_DGM || in->alg > DQ_ADFGM || !pos(in->eps) || !pos(in->Rd) || !pos(in->D_U) ||
+      !std::isfinite(in->lmax_Q) || !std::isfinite(in->normG2) || in->normG2 < 0.0 || !(in->lmin_Q >= 0.0) ||
+      !std::isfinite(in->lmin_Q)) {
+    set_error("dq_theory: invalid algorithm, eps, R_d, D_U or constants");
+    return DQ_ERR_INVALID;
+  }
+  const double rho = std::isnan(in->rho) ? (aug ? 8.0 * in->Rd * in->Rd / in->eps : 0.0) : in->rho;
+  if (!(rho >= 0.0) || !std::isfinite(rho) || (!aug && rho != 0.0)) {
+    set_error("dq_theory: rho must be >= 0 (and 0 for DGM/DFGM)");
+    return DQ_ERR_INVALID;
+  }
+  const double LL = in->lmax_Q + rho * in->normG2, sigma = in->lmin_Q;
+  const double den = in->lmin_Q + rho * in->normG2;
+  if (!(LL > 0.0) || (in->normG2 > 0.0 && !(den > 0.0))) {
+    set_error("dq_theory: L_d is undefined (DGM/DFGM need lmin_Q > 0)");
+    return DQ_ERR_INVALID;
+  }
+  const double Ld = in->normG2 > 0.0 ? in->normG2 / den : 1.0;
+  const double eps = in->eps, Rd = in->Rd, D2 = in->D_U * in->D_U;
+  const double eps_in = fast ? eps * std::sqrt(eps) / (8.0 * Rd * std::sqrt(2.0 * Ld)) : eps / 4.0;
+  const double kout = fast ? std::sqrt(8.0 * Ld * Rd * Rd / eps) : 8.0 * Ld * Rd * Rd / eps;
+  const double kin = sigma > 0.0 ? std::sqrt(LL / sigma) * std::log(LL * D2 / eps_in) + 1.0
+                                 : std::sqrt(2.0 * LL * D2 / eps_in);
+  auto up = [](double v) { return (int64_t)std::max(1.0, std::ceil(v)); };
+  out->rho = rho;
+  out->LL = LL;
+  out->sigma = sigma;
+  out->Ld = Ld;
+  out->eps_in = eps_in;
+  out->k_out = up(kout);
+  out->k_in = up(kin);
+  out->k_total = out->k_out * out->k_in;
+  return DQ_OK;
+}
 
 dq_status dq_context_profile(dq_context* ctx, int32_t enable) {
   if (!ctx) {

@@ -68,6 +68,18 @@ class Outputs(ctypes.Structure):
                 ("memory", ctypes.c_int32)]
 
 
+class TheoryIn(ctypes.Structure):
+    _fields_ = [("alg", ctypes.c_int32), ("eps", ctypes.c_double), ("Rd", ctypes.c_double),
+                ("D_U", ctypes.c_double), ("lmax_Q", ctypes.c_double), ("lmin_Q", ctypes.c_double),
+                ("normG2", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class TheoryOut(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_double), ("LL", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("Ld", ctypes.c_double), ("eps_in", ctypes.c_double), ("k_out", ctypes.c_int64),
+                ("k_in", ctypes.c_int64), ("k_total", ctypes.c_int64)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("gemv_launches", ctypes.c_int64), ("gemv_ms", ctypes.c_double),
                 ("gemv_bytes", ctypes.c_double), ("reduce_launches", ctypes.c_int64),
@@ -77,7 +89,7 @@ class Stats(ctypes.Structure):
 SYMBOLS = ("dq_context_create", "dq_context_destroy", "dq_problem_create", "dq_problem_set_vectors",
            "dq_problem_constants", "dq_problem_destroy", "dq_solve", "dq_solve_many", "dq_serve_start",
            "dq_submit", "dq_poll", "dq_serve_stop", "dq_context_profile", "dq_context_stats",
-           "dq_autotune", "dq_solve_noalloc", "dq_test_tc_gemm", "dq_last_error", "dq_version")
+           "dq_autotune", "dq_solve_noalloc", "dq_test_tc_gemm", "dq_theory", "dq_last_error", "dq_version")
 
 _lib = None
 
@@ -121,12 +133,21 @@ def lib(build_if_needed: bool = True):
     L.dq_solve_noalloc.argtypes = [ctypes.c_int, P(ProblemDesc), P(SolveOpts), P(Outputs), P(Result), vp]
     L.dq_context_profile.argtypes = [vp, ctypes.c_int32]
     L.dq_context_stats.argtypes = [vp, P(Stats), ctypes.c_int32]
+    L.dq_theory.argtypes = [P(TheoryIn), P(TheoryOut)]
     for name in SYMBOLS[:-2]:
         getattr(L, name).restype = st
     L.dq_last_error.restype = ctypes.c_char_p
     L.dq_version.restype = ctypes.c_char_p
     _lib = L
     return L
+
+
+def theory(alg, eps, Rd, D_U, lmax_Q, lmin_Q, normG2, rho=NAN) -> dict:
+    """Iteration counts of the theory mode (dq_theory): rho, LL, sigma, Ld, eps_in, k_out, k_in, k_total."""
+    ti = TheoryIn(ALGS[alg] if isinstance(alg, str) else int(alg), eps, Rd, D_U, lmax_Q, lmin_Q, normG2, rho)
+    to = TheoryOut()
+    check(lib().dq_theory(ctypes.byref(ti), ctypes.byref(to)), (OK,))
+    return {f: getattr(to, f) for f, _ in TheoryOut._fields_}
 
 
 def check(status, allow=(OK, NOT_CONVERGED)):

@@ -453,3 +453,59 @@ def test_step_certificate_run_matches_kkt(alg):
         assert r.infeas_last <= eps and r.f_last - fs <= eps
     if r.converged_avg:
         assert r.infeas_avg <= eps and r.f_avg - fs <= eps
+
+
+# --------------------------------------------------------------- theory mode (Sec. 4-5)
+
+def _theory_counts(qp, alg, inst, eps, Rd, rho=None):
+    c = O.constants(qp, alg, rho=rho, lmin_Q=inst.lmin_Q)
+    D_U = float(np.linalg.norm(inst.ub - inst.lb))
+    ein = O.default_eps_in(alg, eps, c.Ld, Rd)
+    kout = max(1, math.ceil(O.k_out(alg, eps, c.Ld, Rd)))
+    kin = max(1, math.ceil(O.k_in(c.LL, c.sigma, D_U, ein)))
+    return c, kout, kin
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_theory_counts_meet_the_primal_bounds(alg):
+    """With eps_in, k_out of eq. choose_ein, the FOM count k_in of Sec. 5 and lambda^0 = 0, the
+    averaged primal output satisfies the theorems' bounds: (A)DGM dist_K <= eps / R_d and
+    -eps <= F - F* <= eps / 4; (A)DFGM dist_K <= 3 eps / R_d and -3 eps <= F - F* <= 5 eps / 4.
+    R_d = ||lambda*|| and F* come from brute-force KKT; ADGM/ADFGM use rho* = 8 R_d^2 / eps."""
+    eps = 1e-2
+    checked = 0
+    for seed in range(1, 30):
+        inst, qp = _small(seed, n=5, p=4, g_scale=0.02, box=0.3)
+        xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+        Rd = float(np.linalg.norm(lam_s))
+        if Rd < 0.1:
+            continue                      # constraints inactive: nothing to certify
+        rho = O.rho_star(eps, Rd) if alg in (O.ADGM, O.ADFGM) else None
+        c, kout, kin = _theory_counts(qp, alg, inst, eps, Rd, rho)
+        r = O.dfom(qp, alg, c, inner_fixed=kin, outer_fixed=kout)
+        fast = alg in (O.DFGM, O.ADFGM)
+        assert r.infeas_avg <= (3.0 if fast else 1.0) * eps / Rd
+        assert -(3.0 if fast else 1.0) * eps <= r.f_avg - fs <= (1.25 if fast else 0.25) * eps
+        checked += 1
+        if checked == 3:
+            break
+    assert checked == 3
+
+
+def test_rho_star_minimises_the_total_count():
+    """k_out k_in as a function of rho (sigma = 0, the case the optimum is derived for; at
+    least one outer iteration) is smallest at rho* = 8 R_d^2 / eps among a log-spaced sweep:
+    below it the product falls like rho^{-1/4}, above it k_out = 1 and k_in grows."""
+    inst, qp = _small(3, n=5, p=4, g_scale=0.02, box=0.3)
+    eps, Rd = 1e-3, 1.5
+    D_U = float(np.linalg.norm(inst.ub - inst.lb))
+    normG2 = float(np.linalg.norm(inst.G, 2) ** 2)
+    lmax = float(np.linalg.eigvalsh(inst.Q)[-1])
+
+    def total(rho):
+        LL, Ld = lmax + rho * normG2, normG2 / (rho * normG2)      # lambda_min taken as 0
+        ein = O.default_eps_in(O.ADFGM, eps, Ld, Rd)
+        return max(1.0, O.k_out(O.ADFGM, eps, Ld, Rd)) * O.k_in(LL, 0.0, D_U, ein)
+    rhos = O.rho_star(eps, Rd) * np.logspace(-3, 3, 61)
+    best = rhos[int(np.argmin([total(r) for r in rhos]))]
+    assert 0.7 <= best / O.rho_star(eps, Rd) <= 1.5
