@@ -59,8 +59,9 @@ typedef enum { DQ_INNER_GAP = 0, DQ_INNER_FIXED = 1 } dq_inner_stop;
  * 1/(2 L)) when sigma > 0, else the Frank-Wolfe gap; it needs the gradient at
  * x^k (one more G' product when rho > 0).  DQ_CERT_STEP: when sigma > 0, the
  * bound ||L (y - x^k)||^2 (1/(2 sigma) - 1/(2 L)) of the step y^k -> x^k that
- * the iteration makes anyway (no extra product); where sigma = 0, or in the
- * two-pass grid form and the tensor-core batch, the point certificate is used.
+ * the iteration makes anyway (no extra product); where sigma = 0, in the
+ * two-pass grid form, the tensor-core batch and FP32 thread-block solves, the
+ * point certificate is used.
  * DQ_CERT_AUTO (0, the default): the step certificate in the single-pass grid
  * engine, the point certificate in the thread-block engine.  (The gradient at
  * y comes from Q y = Q x^k + beta (Q x^k - Q x^{k-1}), which carries about

@@ -36,7 +36,7 @@ struct CtaInst {
   double rho;                     // NaN: 0 for DGM/DFGM, 1/||G||^2 for ADGM/ADFGM
   double LL, sigma, Ld;           // NaN: derived (Sec. 3 Step 1, eq. Ld)
   int inner_fixed, inner_check_every, max_inner;
-  int cert_step;                  // 1: step certificate of y^k -> x^k where sigma > 0
+  int cert_step;                  // 1: step certificate of y^k -> x^k (FP64, sigma > 0)
   double eps_in;
   int outer_fixed, check_every, max_outer;
   double eps_out;
@@ -217,16 +217,10 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
   const double beta_sigma = (sqrt(I.LL) - sqrt(I.sigma)) / (sqrt(I.LL) + sqrt(I.sigma));
   double theta = 1.0, beta = 0.0;
   const int m = I.inner_check_every > 0 ? I.inner_check_every : 1;
-  // step certificate (sigma > 0): ||L (y^k - x^k)||^2 (1/(2 sigma) - 1/(2 L))
-  // bounds phi(x^k) - phi*, from the step the iteration makes anyway
-  const bool step_cert = I.cert_step && I.sigma > 0.0 && I.inner_fixed <= 0;
-  const double ccoef = I.LL * I.LL * (0.5 / I.sigma - 0.5 / I.LL);
   int k = 0;
   for (;;) {
     ++k;
     const T b = T(beta);
-    const bool check = I.inner_fixed <= 0 && k % m == 0;
-    T sq = T(0);  // a thread's few columns; FP64 only in the block sum
     if (aug) {  // w = [mu + rho (G y + g)]_+ ,  tn = G' w
       for (int j = threadIdx.x; j < p; j += blockDim.x) {
         const T Gy = S.Gx[j] + b * (S.Gx[j] - S.Gxp[j]);
@@ -238,22 +232,40 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
       __syncthreads();
     }
     // step 1 of FOM: x^k = [y - grad phi(y) / L]_U
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const T y = S.x[i] + b * (S.x[i] - S.xp[i]);
-      const T Qy = S.Qx[i] + b * (S.Qx[i] - S.Qxp[i]);
-      const T gr = aug ? Qy + I.q[i] + W.tn[i] : Qy + W.c[i];
-      const T st = gr / L, s = y - st;
-      const T xn = clampT(s, I.lb[i], I.ub[i]);
-      S.xn[i] = xn;
-      if (step_cert && check) {
-        // y - x^k is the step itself where the box is inactive: taking it from
-        // the gradient avoids the cancellation y - x^k, whose rounding
-        // (ulp(y)) times L^2 / (2 sigma) would floor the bound
-        const T d = (s > I.lb[i] && s < I.ub[i]) ? st : y - xn;
-        sq += d * d;
+    auto plain_step = [&]() {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const T y = S.x[i] + b * (S.x[i] - S.xp[i]);
+        const T Qy = S.Qx[i] + b * (S.Qx[i] - S.Qxp[i]);
+        const T gr = aug ? Qy + I.q[i] + W.tn[i] : Qy + W.c[i];
+        S.xn[i] = clampT(y - gr / L, I.lb[i], I.ub[i]);
       }
+    };
+    if constexpr (sizeof(T) == 8) {
+      // FP64: the step certificate ||L (y^k - x^k)||^2 (1/(2 sigma) - 1/(2 L))
+      // bounds phi(x^k) - phi* from the step itself; its sum waits in W.red[32].
+      // (FP32 keeps the certificate at x^k: the extrapolated Q y carries about
+      // (1 + 2 beta) times the rounding of one product, which the step
+      // certificate squares.)
+      if (I.cert_step && I.sigma > 0.0 && I.inner_fixed <= 0 && k % m == 0) {
+        T sq = T(0);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          const T y = S.x[i] + b * (S.x[i] - S.xp[i]);
+          const T Qy = S.Qx[i] + b * (S.Qx[i] - S.Qxp[i]);
+          const T gr = aug ? Qy + I.q[i] + W.tn[i] : Qy + W.c[i];
+          const T st = gr / L, s = y - st;
+          const T xn = clampT(s, I.lb[i], I.ub[i]);
+          S.xn[i] = xn;
+          // y - x^k is the step itself where the box is inactive (no cancellation)
+          const T d = (s > I.lb[i] && s < I.ub[i]) ? st : y - xn;
+          sq += d * d;
+        }
+        block_sum(double(sq), W.red);
+      } else {
+        plain_step();
+      }
+    } else {
+      plain_step();
     }
-    const double cstep = (step_cert && check) ? ccoef * block_sum(double(sq), W.red) : 0.0;
     __syncthreads();
     mtv<T>(W.Q, n, n, n, S.xn, S.Qxn, W.part);
     if (aug) {
@@ -276,8 +288,14 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
     if (I.inner_fixed > 0) {
       if (k >= I.inner_fixed) break;
     } else {
-      if (check) {
-        const double cert = step_cert ? cstep : cta_cert(I, W, S.x, S.Qx, S.Gx, mu, !aug);
+      if (k % m == 0) {
+        double cert;
+        if constexpr (sizeof(T) == 8) {
+          cert = (I.cert_step && I.sigma > 0.0) ? I.LL * I.LL * (0.5 / I.sigma - 0.5 / I.LL) * W.red[32]
+                                                : cta_cert(I, W, S.x, S.Qx, S.Gx, mu, !aug);
+        } else {
+          cert = cta_cert(I, W, S.x, S.Qx, S.Gx, mu, !aug);
+        }
         if (cert <= I.eps_in) break;
       }
       if (k >= I.max_inner) break;
