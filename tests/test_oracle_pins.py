@@ -509,3 +509,23 @@ def test_rho_star_minimises_the_total_count():
     rhos = O.rho_star(eps, Rd) * np.logspace(-3, 3, 61)
     best = rhos[int(np.argmin([total(r) for r in rhos]))]
     assert 0.7 <= best / O.rho_star(eps, Rd) <= 1.5
+
+
+@pytest.mark.parametrize("rho,cone", [(0.0, O.CONE_INEQ), (0.7, O.CONE_INEQ), (0.7, O.CONE_EQ)])
+def test_sampled_step_matches_the_c_oracle(rho, cone):
+    """The sampled FOM step (numpy, used at full size) equals one GM step of the C oracle from
+    the same point, at every coordinate and at a sampled subset."""
+    inst, _ = _small(8, n=9, p=6, g_scale=0.02, box=0.5)
+    qp = _qp(inst, cone)
+    rng = np.random.default_rng(2)
+    y = rng.uniform(-0.5, 0.5, 9)
+    mu = np.abs(rng.standard_normal(6)) if cone == O.CONE_INEQ else rng.standard_normal(6)
+    LL = 40.0
+    x1, _, _ = O.fom(qp, rho, mu, LL, 0.0, y, fixed=1, variant=O.INNER_GM)
+    full = O.sampled_fom_step(q=inst.q, g=inst.g, G=inst.G, Q_rows=None, rows=None, y=y, mu=mu, rho=rho,
+                              L=LL, lb=inst.lb, ub=inst.ub, Qy_full=inst.Q @ y, cone=cone)
+    np.testing.assert_allclose(full, x1, rtol=0, atol=1e-14)
+    rows = np.array([0, 3, 4, 8])
+    part = O.sampled_fom_step(q=inst.q, g=inst.g, G=inst.G, Q_rows=inst.Q[rows], rows=rows, y=y, mu=mu,
+                              rho=rho, L=LL, lb=inst.lb, ub=inst.ub, cone=cone)
+    np.testing.assert_allclose(part, x1[rows], rtol=0, atol=1e-14)
