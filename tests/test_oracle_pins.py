@@ -529,3 +529,164 @@ def test_sampled_step_matches_the_c_oracle(rho, cone):
     part = O.sampled_fom_step(q=inst.q, g=inst.g, G=inst.G, Q_rows=inst.Q[rows], rows=rows, y=y, mu=mu,
                               rho=rho, L=LL, lb=inst.lb, ub=inst.ub, cone=cone)
     np.testing.assert_allclose(part, x1[rows], rtol=0, atol=1e-14)
+
+
+# ------------------------------------------ the last primal iterate (eq. last_primal, Sec. 4.1)
+
+def _dual_value_lbfgsb(qp, rho, lam):
+    """d_rho(lam) = min over the box of L_rho(., lam) (eq. dual_fc) by scipy's L-BFGS-B: a route
+    that shares nothing with Algorithm FOM (value and gradient of eq. auglag1 are pinned above
+    against the minimum over s and against finite differences)."""
+    from scipy.optimize import minimize
+    f = lambda u: O.lagrangian(qp, rho, u, lam)
+    jac = lambda u: O.grad_lagr(qp, rho, u, lam)
+    best = None
+    for x0 in (np.zeros(qp.n), 0.5 * (qp.lb + qp.ub) + 0.25 * (qp.ub - qp.lb)):
+        m = minimize(f, x0, jac=jac, bounds=list(zip(qp.lb, qp.ub)), method="L-BFGS-B",
+                     options=dict(ftol=1e-16, gtol=1e-13, maxiter=20000, maxcor=30))
+        if best is None or m.fun < best.fun:
+            best = m
+    return float(best.fun), best.x
+
+
+def _lambda_after(qp, alg, c, k, **kw):
+    """lambda^k of Algorithm DFOM (lambda^0 = 0 for k = 0)."""
+    if k == 0:
+        return np.zeros(qp.p)
+    return O.dfom(qp, alg, c, outer_fixed=k, want_avg=False, **kw).lam
+
+
+def _active_instance(seed=31):
+    # constraints active at the optimum and the box partly active, so lambda^k moves over
+    # many outer iterations and ubar(lambda^k) differs from ubar(mu^k) far from convergence
+    inst, qp = _small(seed, n=6, p=5, g_scale=0.02, box=0.4)
+    return inst, qp
+
+
+@pytest.mark.parametrize("alg", [O.DFGM, O.ADFGM])
+def test_fast_last_iterate_solves_the_inner_problem_at_lambda_k(alg):
+    """eq. last_primal for DFGM/ADFGM: the last primal output is ubar(lambda^k), an
+    eps_in-solution (eq. duquad_in) of the inner problem at the last dual iterate lambda^k,
+    not the chain iterate ubar^k = ubar(mu^k).  Checked far from convergence against d_rho
+    from L-BFGS-B, with mu^k = lambda^{k-1} + beta_{k-1} (lambda^{k-1} - lambda^{k-2})."""
+    inst, qp = _active_instance()
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    eps_in = 1e-7
+    kw = dict(eps_in=eps_in, max_inner=200000)
+    checked = 0
+    for k in (3, 5, 8):
+        r = O.dfom(qp, alg, c, outer_fixed=k, want_avg=False, trace_cap=k, **kw)
+        ru = O.dfom(qp, alg, c, outer_fixed=k, want_last=False, **kw)   # x_last = ubar^k then
+        lam_k = r.lam
+        np.testing.assert_array_equal(lam_k, ru.lam)                      # the extra solve leaves the chain alone
+        lam_1, lam_2 = _lambda_after(qp, alg, c, k - 1, **kw), _lambda_after(qp, alg, c, k - 2, **kw)
+        mu_k = lam_1 + r.trace[k - 2, 3] * (lam_1 - lam_2)
+        d_lam, _ = _dual_value_lbfgsb(qp, c.rho, lam_k)
+        d_mu, _ = _dual_value_lbfgsb(qp, c.rho, mu_k)
+        sub_last = O.lagrangian(qp, c.rho, r.x_last, lam_k) - d_lam
+        assert -1e-10 <= sub_last <= eps_in + 1e-10
+        assert O.inner_cert(qp, c.rho, r.x_last, lam_k, c.LL, c.sigma) <= eps_in
+        # ubar^k solves the inner problem at mu^k, and is far from solving it at lambda^k
+        assert O.lagrangian(qp, c.rho, ru.x_last, mu_k) - d_mu <= eps_in + 1e-10
+        assert O.lagrangian(qp, c.rho, ru.x_last, lam_k) - d_lam > 100 * eps_in
+        # and the last output is not an eps_in-solution at mu^k
+        assert O.lagrangian(qp, c.rho, r.x_last, mu_k) - d_mu > 100 * eps_in
+        checked += 1
+    assert checked == 3
+
+
+@pytest.mark.parametrize("alg", [O.DGM, O.ADGM])
+def test_dgm_last_iterate_is_the_chain_iterate(alg):
+    """eq. last_primal for DGM/ADGM: mu^{k+1} = lambda^k (beta = 0), so the last primal iterate
+    is the inner solution the chain computes, ubar^k, with no extra solve."""
+    inst, qp = _active_instance()
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    for k in (1, 4, 9):
+        r = O.dfom(qp, alg, c, eps_in=1e-7, outer_fixed=k, want_avg=False)
+        ru = O.dfom(qp, alg, c, eps_in=1e-7, outer_fixed=k, want_last=False)
+        np.testing.assert_array_equal(r.x_last, ru.x_last)
+        assert r.inner_iters == ru.inner_iters
+
+
+@pytest.mark.parametrize("alg", [O.DFGM, O.ADFGM])
+def test_fast_last_iterate_warm_starts_from_ubar_k(alg):
+    """The extra inner solve of eq. last_primal is Algorithm FOM at mu = lambda^k started from
+    ubar^k (the warm start of Sec. 3): with one inner iteration it is the projected gradient
+    step [ubar^k - grad_u L_rho(ubar^k, lambda^k) / L_L]_U.  Starting it from 0, from
+    ubar^{k-1} or taking the gradient at mu^k gives other points, which this separates."""
+    inst, qp = _active_instance()
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    for k in (2, 6):
+        r = O.dfom(qp, alg, c, inner_fixed=1, outer_fixed=k, want_avg=False, trace_cap=k)
+        ubar_k = O.dfom(qp, alg, c, inner_fixed=1, outer_fixed=k, want_last=False).x_last
+        ubar_km1 = O.dfom(qp, alg, c, inner_fixed=1, outer_fixed=k - 1, want_last=False).x_last
+        lam_k = r.lam
+        lam_1 = _lambda_after(qp, alg, c, k - 1, inner_fixed=1)
+        lam_2 = _lambda_after(qp, alg, c, k - 2, inner_fixed=1)
+        mu_k = lam_1 + r.trace[k - 2, 3] * (lam_1 - lam_2)
+
+        def step(x, lam):
+            return np.clip(x - O.grad_lagr(qp, c.rho, x, lam) / c.LL, qp.lb, qp.ub)
+        np.testing.assert_allclose(r.x_last, step(ubar_k, lam_k), rtol=0, atol=1e-14)
+        for wrong in (step(np.zeros(qp.n), lam_k), step(ubar_km1, lam_k), step(ubar_k, mu_k)):
+            assert np.max(np.abs(wrong - r.x_last)) > 1e-6
+
+
+@pytest.mark.parametrize("alg", ALGS)
+def test_last_iterate_feasibility_and_suboptimality_links(alg):
+    """Sec. 4.1, proof of the last-iterate theorem, at every k for the multiplier lam at which
+    the last output ubar(lam) was computed (lam = lambda^k for (A)DFGM, mu^k = lambda^{k-1} for
+    (A)DGM), with F*, lambda* from brute-force KKT and d_rho(lam) from L-BFGS-B:
+      eq. aux_feas_bound   dist_K(G u + g) <= sqrt(2 L_d eps_in) + sqrt(2 L_d (F* - d(lam)))
+      eq. aux_subopt_right F(u) - F* <= ||lam|| (sqrt(2 L_d eps_in) + sqrt(2 L_d (F* - d(lam)))) + eps_in
+      eq. psubopt_left     F(u) - F* >= -||lambda*|| dist_K(G u + g)."""
+    inst, qp = _active_instance()
+    xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+    assert np.linalg.norm(lam_s) > 0.1                    # the instance has active constraints
+    c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+    eps_in = 1e-6
+    fast = alg in (O.DFGM, O.ADFGM)
+    tight = 0
+    for k in (1, 2, 4, 8, 16, 32):
+        r = O.dfom(qp, alg, c, eps_in=eps_in, outer_fixed=k, want_avg=False, max_inner=200000)
+        lam = r.lam if fast else _lambda_after(qp, alg, c, k - 1, eps_in=eps_in, max_inner=200000)
+        d_lam, _ = _dual_value_lbfgsb(qp, c.rho, lam)
+        gap = max(fs - d_lam, 0.0)
+        inf = O.infeas(qp, r.x_last)
+        link = math.sqrt(2 * c.Ld * eps_in) + math.sqrt(2 * c.Ld * gap)
+        assert inf <= link + 1e-9
+        assert r.f_last - fs <= np.linalg.norm(lam) * link + eps_in + 1e-9
+        assert r.f_last - fs >= -np.linalg.norm(lam_s) * inf - 1e-9
+        tight += inf >= 0.05 * link
+    assert tight > 0                                       # the feasibility link is not vacuous here
+
+
+@pytest.mark.parametrize("alg", [O.DGM, O.DFGM])
+def test_last_iterate_theorem_at_k_out(alg):
+    """The last-iterate theorem (Sec. 4.1, eq. pfeas_subopt_final and the |F - F*| bound after
+    it): with eps_in and k_out of eq. choose_ein (R_d = ||lambda*||, lambda^0 = 0), ubar(lambda^k_out)
+    satisfies dist_K <= max{(L_d eps)^{1/2}/sqrt(2), L_d^{1/4} eps^{3/4}/(3 R_d)^{1/2}} + (2 L_d eps)^{1/2}
+    and |F - F*| <= 4 R_d max{...} + 4 R_d (2 L_d eps)^{1/2} + eps_in, given F* - d(lambda^k_out) <= eps."""
+    eps = 1e-3
+    checked = 0
+    for seed in range(31, 60):
+        inst, qp = _small(seed, n=6, p=5, g_scale=0.02, box=0.4)
+        xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+        Rd = float(np.linalg.norm(lam_s))
+        if Rd < 0.1:
+            continue
+        c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+        ein = O.default_eps_in(alg, eps, c.Ld, Rd)
+        kout = max(1, math.ceil(O.k_out(alg, eps, c.Ld, Rd)))
+        r = O.dfom(qp, alg, c, eps_in=ein, outer_fixed=kout, want_avg=False, max_inner=200000)
+        lam = r.lam if alg == O.DFGM else _lambda_after(qp, alg, c, kout - 1, eps_in=ein, max_inner=200000)
+        d_lam, _ = _dual_value_lbfgsb(qp, c.rho, lam)
+        assert fs - d_lam <= eps                          # eq. bound_gen_dfg at k_out
+        m = max(math.sqrt(c.Ld * eps) / math.sqrt(2.0), c.Ld ** 0.25 * eps ** 0.75 / math.sqrt(3.0 * Rd))
+        feas = m + math.sqrt(2.0 * c.Ld * eps)
+        assert O.infeas(qp, r.x_last) <= feas
+        assert abs(r.f_last - fs) <= 4.0 * Rd * m + 4.0 * Rd * math.sqrt(2.0 * c.Ld * eps) + ein
+        checked += 1
+        if checked == 3:
+            break
+    assert checked == 3
