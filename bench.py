@@ -37,9 +37,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QP solves/s at eps=1e-3"
 # DRAM bytes (read + write) per algorithmic byte of the large-dense kernels, each from one ncu
-# capture (profiles/k_v2_pass_large_dense.md at n = 12000, profiles/k_rows_large_dense.md at
-# n = 8192), applied to the full-size launches: both kernels read every matrix element once, so
-# traffic grows in proportion to the bytes a launch processes
+# capture (k_v2_pass at n = 12000, k_rows at n = 8192), applied to the full-size launches: both
+# kernels read every matrix element once, so traffic grows in proportion to the bytes a launch
+# processes
 TRAFFIC_RATIO = {"k_v2_pass": 1.0055, "k_rows": 1.0115}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 

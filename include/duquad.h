@@ -89,7 +89,7 @@ typedef enum {
   DQ_ERR_NOMEM = -2,     /* device allocation failed                          */
   DQ_ERR_CUDA = -3,      /* CUDA runtime error                                */
   DQ_ERR_NONFINITE = -4, /* NaN/Inf appeared in the iterates                  */
-  DQ_ERR_DIVERGED = -5,  /* ||lambda|| grew past the divergence bound         */
+  DQ_ERR_DIVERGED = -5,  /* infeasible: certified d_lb > max of F on the box  */
   DQ_ERR_TIMEOUT = -6,   /* a bounded device-side wait gave up                */
   DQ_ERR_REJECTED = -7   /* serving: admission refused (footprint / queue)    */
 } dq_status;
@@ -97,13 +97,30 @@ typedef enum {
 typedef struct dq_context dq_context;
 typedef struct dq_problem dq_problem;
 
+/* How lambda_max(Q) and ||G||^2 = lambda_max(G'G) are found when
+ * dq_problem_desc leaves them NaN (they set L_L of Sec. 3 Step 1 and L_d of
+ * eq. Ld, which Algorithm FOM's step 1/L_L and both inner certificates need
+ * as upper bounds of the Lipschitz constants).
+ *   DQ_LIP_LANCZOS (0, default): the Lanczos method on the GPU from a
+ *     pseudo-random (SplitMix64) start vector for k = ceil((ln(1.648 sqrt(n) /
+ *     1e-3) / 0.1 + 1) / 2) steps (all n when n is smaller), products in the
+ *     problem's precision, the tridiagonal eigenproblem in FP64, returning
+ *     max(theta + 2 r, theta / 0.99) for the top Ritz value theta and its
+ *     residual r.  By Kuczynski and Wozniakowski's bound for random starts
+ *     (SIAM J. Matrix Anal. Appl. 13(4), 1992) theta >= 0.99 lambda_max except
+ *     with probability <= 1e-3, so the value is an upper bound except with
+ *     that probability, and about 1 % above lambda_max.
+ *   DQ_LIP_BOUND: guaranteed bounds, min(Gershgorin row sum, ||Q||_F) and
+ *     min(||G||_1 ||G||_inf, ||G||_F^2) in FP64; often far above the true
+ *     values (slower convergence), for callers that need a certain bound. */
+typedef enum { DQ_LIP_LANCZOS = 0, DQ_LIP_BOUND = 1 } dq_lipschitz;
+
 /* Problem description (eq. original_primal).  batch > 1 describes `batch`
  * instances that share Q and G and differ in q (batch x n) and g (batch x p),
  * all row-major.  lmax_Q, lmin_Q, normG2: NaN means "compute"; lmax_Q and
- * normG2 are then found by FP64 power iteration on the GPU (Rayleigh quotient
- * plus residual norm, so an upper estimate), lmin_Q is taken as 0 (valid for
- * rho > 0 only).  A given value is used verbatim; lmin_Q must be a lower bound
- * of lambda_min(Q) (it sets sigma_L and L_d of eq. Ld). */
+ * normG2 are then found on the GPU as `lipschitz` says, lmin_Q is taken as 0
+ * (valid for rho > 0 only).  A given value is used verbatim; lmin_Q must be a
+ * lower bound of lambda_min(Q) (it sets sigma_L and L_d of eq. Ld). */
 typedef struct {
   int32_t n, p;            /* variables, linear constraints (p >= 0)           */
   int32_t batch;           /* >= 1                                             */
@@ -112,6 +129,7 @@ typedef struct {
   int32_t memory;          /* dq_memory of the arrays below                    */
   const void *Q, *q, *G, *g, *lb, *ub;
   double lmax_Q, lmin_Q, normG2;
+  int32_t lipschitz;       /* dq_lipschitz (default DQ_LIP_LANCZOS)            */
 } dq_problem_desc;
 
 /* Solve options.  NaN / 0 fields take the documented defaults. */
@@ -219,12 +237,20 @@ dq_status dq_solve_many(dq_problem *const *probs, int32_t count, const dq_solve_
  * Limits: n * p elements of G must fit the scratch (8 MiB minus 4 KiB:
  * n * p <= 1048064 for FP64, 2096128 for FP32) and the instance's vectors one
  * thread block's shared memory; otherwise DQ_ERR_INVALID with a message.
- * No warm start.  The first call on a device looks up the scratch's address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call shares the one scratch array, so
- * calls whose GPU work overlaps (other streams or threads on the same device)
- * race: serialise them.  stream: cudaStream_t (NULL = legacy default);
- * synchronises it before returning. */
+ * No warm start.
+ * Set-up: the first call on a device looks up the scratch's device address
+ * (cudaGetSymbolAddress, with that device current).  Under CUDA's default
+ * lazy module loading that first call (or the first launch) is also when the
+ * library's kernels and the 8 MiB array are placed on the device, so it can
+ * fail with an out-of-memory error if the caller's pool has already reserved
+ * the GPU: make one call per device before any pool reserves device memory
+ * (or run with CUDA_MODULE_LOADING=EAGER, which places them when the library
+ * loads).  After that first call, calls allocate nothing.
+ * Every call copies its descriptor from host memory and synchronises
+ * `stream` before returning.  Every call shares the one
+ * scratch array (which keeps the last call's contents), so calls whose GPU
+ * work overlaps (other streams or threads on the same device) race:
+ * serialise them.  stream: cudaStream_t (NULL = legacy default). */
 dq_status dq_solve_noalloc(int device, const dq_problem_desc *desc, const dq_solve_opts *opts,
                            const dq_outputs *out, dq_result *result, void *cuda_stream);
 

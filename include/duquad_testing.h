@@ -31,6 +31,17 @@ extern "C" {
 dq_status dq_test_tc_gemm(const float *A, const float *B, float *D, int32_t M, int32_t N, int32_t K,
                           int32_t split, int32_t bulk, void *stream);
 
+/* The bounded device-side wait the engines use (an mbarrier phase polled
+ * against the GPU's global timer, as in the single-pass iteration's bulk-copy
+ * ring and the tensor-core batch) in isolation: one thread block waits on an
+ * mbarrier that expects one arrival.  complete != 0: the arrival comes first
+ * and the call returns DQ_OK.  complete == 0: nothing ever arrives, the wait
+ * gives up after limit_ns nanoseconds and the call returns DQ_ERR_TIMEOUT,
+ * leaving the CUDA context usable (nothing hangs or traps).  limit_ns in
+ * (0, 1e9], else DQ_ERR_INVALID.  stream: cudaStream_t (NULL = legacy
+ * default).  Synchronises the stream. */
+dq_status dq_test_bounded_wait(uint64_t limit_ns, int32_t complete, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

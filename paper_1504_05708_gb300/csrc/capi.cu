@@ -33,14 +33,21 @@ void set_error(const char* fmt, ...) {
 
 // ------------------------------------------------------------ small kernels
 
+// Transposed copy of G (p x n -> n x p); flags non-finite entries of G.
 template <typename T>
-__global__ void k_transpose(const T* __restrict__ in, T* __restrict__ out, int rows, int cols) {
+__global__ void k_transpose(const T* __restrict__ in, T* __restrict__ out, int rows, int cols, CheckFlags* f) {
   __shared__ T tile[32][33];
   const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  bool bad = false;
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int r = by + k, c = bx + threadIdx.x;
-    if (r < rows && c < cols) tile[k][threadIdx.x] = in[(size_t)r * cols + c];
+    if (r < rows && c < cols) {
+      const T v = in[(size_t)r * cols + c];
+      bad |= !isfinite(v);
+      tile[k][threadIdx.x] = v;
+    }
   }
+  if (bad) atomicOr(&f->nonfinite, 1);
   __syncthreads();
   for (int k = threadIdx.y; k < 32; k += 8) {
     const int r = bx + k, c = by + threadIdx.x;  // out is cols x rows
@@ -48,9 +55,73 @@ __global__ void k_transpose(const T* __restrict__ in, T* __restrict__ out, int r
   }
 }
 
-__global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, size_t m) {
+// FP64 -> FP32 conversion of an uploaded chunk; flags non-finite values.
+__global__ void k_d2f(const double* __restrict__ in, float* __restrict__ out, size_t m, CheckFlags* f) {
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    bad |= !isfinite(v);
+    out[i] = float(v);
+  }
+  if (bad) atomicOr(&f->nonfinite, 1);
+}
+
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ a, size_t m, CheckFlags* f) {
+  bool bad = false;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = float(in[i]);
+    bad |= !isfinite(a[i]);
+  if (bad) atomicOr(&f->nonfinite, 1);
+}
+
+template <typename T>
+__global__ void k_check_box(const T* __restrict__ lb, const T* __restrict__ ub, int n, CheckFlags* f) {
+  bool bad = false, inv = false;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    bad |= !isfinite(lb[i]) || !isfinite(ub[i]);
+    inv |= !(lb[i] <= ub[i]);
+  }
+  if (bad) atomicOr(&f->nonfinite, 1);
+  if (inv) atomicOr(&f->bad_box, 1);
+}
+
+// Symmetry and finiteness of Q (n x n row-major): block (I, J), J >= I, of
+// 32 x 32 tiles compares Q[I, J] with Q[J, I]' through shared memory (both
+// reads coalesced); a pair fails when |Q_ij - Q_ji| > tol sqrt(|Q_ii Q_jj|)
+// (rounding of a symmetric Q computed as a product scales with its rows'
+// norms, which sqrt(Q_ii Q_jj) is for a PSD Q).  One failing pair is kept.
+template <typename T>
+__global__ void k_check_sym(const T* __restrict__ Q, int n, double tol, CheckFlags* f) {
+  const int I = blockIdx.y, J = blockIdx.x;
+  if (J < I) return;
+  __shared__ T tb[32][33];
+  const int i0 = I * 32, j0 = J * 32;
+  bool bad = false;
+  for (int k = threadIdx.y; k < 32; k += 8) {  // tb[k][c] = Q[j0 + k][i0 + c]
+    const int r = j0 + k, c = i0 + threadIdx.x;
+    if (r < n && c < n) {
+      const T v = Q[(size_t)r * n + c];
+      tb[k][threadIdx.x] = v;
+      bad |= !isfinite(v);
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {  // a = Q[i0 + k][j0 + c], b = Q[j0 + c][i0 + k]
+    const int i = i0 + k, j = j0 + threadIdx.x;
+    if (i < n && j < n) {
+      const T a = Q[(size_t)i * n + j];
+      const T b = tb[threadIdx.x][k];
+      if (I != J) bad |= !isfinite(a);
+      const double lim = tol * sqrt(fabs(double(Q[(size_t)i * n + i])) * fabs(double(Q[(size_t)j * n + j])));
+      if (!(fabs(double(a) - double(b)) <= lim) && isfinite(a) && isfinite(b)) {
+        if (atomicCAS(&f->asym, 0, 1) == 0) {
+          f->asym_i = i;
+          f->asym_j = j;
+        }
+      }
+    }
+  }
+  if (bad) atomicOr(&f->nonfinite, 1);
 }
 
 dq_status ctx_scratch(dq_context* ctx, size_t bytes, void** out) {
@@ -84,41 +155,110 @@ static dq_status dalloc(void** p, size_t bytes) {
   return DQ_OK;
 }
 
-// Copy `m` elements into device array `dst` of the problem's element type.
-// src: host double (memory = DQ_HOST) or device array of the element type.
-static dq_status upload(dq_problem* P, void* dst, const void* src, size_t m, int memory) {
-  cudaStream_t st = P->ctx->stream;
-  if (m == 0) return DQ_OK;
-  if (memory == DQ_DEVICE) {
-    DQ_CK(cudaMemcpyAsync(dst, src, m * P->esz, cudaMemcpyDeviceToDevice, st));
-    return DQ_OK;
+// Upload resources of the context: staging halves of kStageChunk doubles, the
+// copy stream, its events and the validation flags (created on first use).
+static constexpr size_t kStageChunk = size_t(4) << 20;  // 32 MiB of doubles per half
+
+// Symmetry tolerance of Q relative to sqrt(|Q_ii Q_jj|): rounding of the
+// stored type (a symmetric FP64 Q rounds to a symmetric or one-ulp-apart
+// FP32 pair) plus the rounding of a Q formed as a product in FP64.
+static constexpr double kSymTol32 = 1e-6, kSymTol64 = 1e-10;
+
+static dq_status upload_setup(dq_context* ctx, bool stage) {
+  if (!ctx->dflags) {
+    if (cudaMalloc(&ctx->dflags, sizeof(CheckFlags)) != cudaSuccess ||
+        cudaMallocHost(&ctx->hflags, sizeof(CheckFlags)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("validation flag allocation failed");
+      return DQ_ERR_NOMEM;
+    }
   }
-  if (P->esz == 8) {
-    DQ_CK(cudaMemcpyAsync(dst, src, m * 8, cudaMemcpyHostToDevice, st));
-    return DQ_OK;
-  }
-  void* tmp = nullptr;
-  dq_status s = dalloc(&tmp, m * 8);
-  if (s != DQ_OK) return s;
-  cudaError_t e = cudaMemcpyAsync(tmp, src, m * 8, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) {
-    k_d2f<<<1024, 256, 0, st>>>((const double*)tmp, (float*)dst, m);
-    ++P->ctx->launches;
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(tmp);
-  if (e != cudaSuccess) {
-    set_error("upload failed: %s", cudaGetErrorString(e));
-    return DQ_ERR_CUDA;
+  if (stage && !ctx->stage) {
+    if (cudaMalloc(&ctx->stage, 2 * kStageChunk * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->stage = nullptr;
+      set_error("upload staging allocation failed");
+      return DQ_ERR_NOMEM;
+    }
+    ctx->stage_bytes = 2 * kStageChunk * sizeof(double);
+    DQ_CK(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : ctx->cev) DQ_CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   return DQ_OK;
 }
 
-static bool host_all_finite(const double* a, size_t m) {
-  for (size_t i = 0; i < m; ++i)
-    if (!isfinite(a[i])) return false;
-  return true;
+// Copy `m` elements into device array `dst` of the problem's element type.
+// src: host double (memory = DQ_HOST) or device array of the element type.
+// Values are checked for finiteness on the device (flags in ctx->dflags).
+// Host doubles for a float problem go through the context's staging halves
+// in chunks: the copy of chunk k (copy stream) overlaps the conversion of
+// chunk k - 1 (the context's stream); everything is ordered on the context's
+// stream when this returns (no host synchronisation here).
+static dq_status upload(dq_problem* P, void* dst, const void* src, size_t m, int memory) {
+  dq_context* ctx = P->ctx;
+  cudaStream_t st = ctx->stream;
+  if (m == 0) return DQ_OK;
+  CheckFlags* fl = (CheckFlags*)ctx->dflags;
+  const unsigned grid = (unsigned)std::min<size_t>((m + 255) / 256, 2048);
+  if (memory == DQ_DEVICE || P->esz == 8) {
+    DQ_CK(cudaMemcpyAsync(dst, src, m * P->esz,
+                          memory == DQ_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (P->esz == 8) k_check_finite<double><<<grid, 256, 0, st>>>((const double*)dst, m, fl);
+    else k_check_finite<float><<<grid, 256, 0, st>>>((const float*)dst, m, fl);
+    ++ctx->launches;
+    DQ_CK(cudaGetLastError());
+    return DQ_OK;
+  }
+  dq_status s = upload_setup(ctx, true);
+  if (s != DQ_OK) return s;
+  double* half[2] = {(double*)ctx->stage, (double*)ctx->stage + kStageChunk};
+  cudaEvent_t* copied = ctx->cev;      // [0], [1]
+  cudaEvent_t* freed = ctx->cev + 2;   // [2], [3]
+  // the halves are free once earlier work on the context's stream is done
+  DQ_CK(cudaEventRecord(freed[0], st));
+  DQ_CK(cudaEventRecord(freed[1], st));
+  for (size_t off = 0, k = 0; off < m; off += kStageChunk, ++k) {
+    const size_t cnt = std::min(kStageChunk, m - off);
+    const int b = (int)(k & 1);
+    DQ_CK(cudaStreamWaitEvent(ctx->cstream, freed[b], 0));
+    DQ_CK(cudaMemcpyAsync(half[b], (const double*)src + off, cnt * 8, cudaMemcpyHostToDevice, ctx->cstream));
+    DQ_CK(cudaEventRecord(copied[b], ctx->cstream));
+    DQ_CK(cudaStreamWaitEvent(st, copied[b], 0));
+    k_d2f<<<(unsigned)std::min<size_t>((cnt + 255) / 256, 4096), 256, 0, st>>>(half[b], (float*)dst + off, cnt, fl);
+    ++ctx->launches;
+    DQ_CK(cudaGetLastError());
+    DQ_CK(cudaEventRecord(freed[b], st));
+  }
+  return DQ_OK;
+}
+
+// Clear the validation flags (before a create / set_vectors).
+static dq_status flags_clear(dq_context* ctx) {
+  dq_status s = upload_setup(ctx, false);
+  if (s != DQ_OK) return s;
+  DQ_CK(cudaMemsetAsync(ctx->dflags, 0, sizeof(CheckFlags), ctx->stream));
+  return DQ_OK;
+}
+
+// Read the validation flags (synchronises the context's stream).
+static dq_status flags_check(dq_context* ctx) {
+  DQ_CK(cudaMemcpyAsync(ctx->hflags, ctx->dflags, sizeof(CheckFlags), cudaMemcpyDeviceToHost, ctx->stream));
+  DQ_CK(cudaStreamSynchronize(ctx->stream));
+  const CheckFlags& f = *(const CheckFlags*)ctx->hflags;
+  if (f.nonfinite) {
+    set_error("non-finite value in the problem data");
+    return DQ_ERR_INVALID;
+  }
+  if (f.bad_box) {
+    set_error("lb > ub for some coordinate");
+    return DQ_ERR_INVALID;
+  }
+  if (f.asym) {
+    set_error("Q is not symmetric: |Q[%d][%d] - Q[%d][%d]| exceeds the tolerance", f.asym_i, f.asym_j, f.asym_j,
+              f.asym_i);
+    return DQ_ERR_INVALID;
+  }
+  return DQ_OK;
 }
 
 void fill_result(dq_result* r, const DevResult& d, const double* consts, const SolveCfg& c) {
@@ -318,6 +458,15 @@ static void context_free(dq_context* ctx) {
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->cstream) {
+    cudaStreamSynchronize(ctx->cstream);
+    cudaStreamDestroy(ctx->cstream);
+  }
+  for (cudaEvent_t e : ctx->cev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->stage) cudaFree(ctx->stage);
+  if (ctx->dflags) cudaFree(ctx->dflags);
+  if (ctx->hflags) cudaFreeHost(ctx->hflags);
   delete ctx;
 }
 
@@ -358,26 +507,15 @@ dq_status dq_problem_create(dq_context* ctx, const dq_problem_desc* d, dq_proble
     set_error("unknown memory kind %d", d->memory);
     return DQ_ERR_INVALID;
   }
+  if (d->lipschitz != DQ_LIP_LANCZOS && d->lipschitz != DQ_LIP_BOUND) {
+    set_error("unknown lipschitz mode %d", d->lipschitz);
+    return DQ_ERR_INVALID;
+  }
   if (!d->Q || !d->q || !d->lb || !d->ub || (d->p > 0 && (!d->G || !d->g))) {
     set_error("NULL problem array");
     return DQ_ERR_INVALID;
   }
   const size_t n = d->n, p = d->p, B = d->batch;
-  if (d->memory == DQ_HOST) {
-    const double* lb = (const double*)d->lb;
-    const double* ub = (const double*)d->ub;
-    for (size_t i = 0; i < n; ++i)
-      if (!(lb[i] <= ub[i])) {
-        set_error("lb[%zu] > ub[%zu] or NaN", i, i);
-        return DQ_ERR_INVALID;
-      }
-    if (!host_all_finite((const double*)d->Q, n * n) || !host_all_finite((const double*)d->q, B * n) ||
-        (p && (!host_all_finite((const double*)d->G, p * n) || !host_all_finite((const double*)d->g, B * p))) ||
-        !host_all_finite(lb, n) || !host_all_finite(ub, n)) {
-      set_error("non-finite value in the problem data");
-      return DQ_ERR_INVALID;
-    }
-  }
   if (!isnan(d->lmin_Q) && d->lmin_Q < 0) {
     set_error("lmin_Q must be a lower bound >= 0");
     return DQ_ERR_INVALID;
@@ -397,11 +535,13 @@ dq_status dq_problem_create(dq_context* ctx, const dq_problem_desc* d, dq_proble
   P->normG2 = d->normG2;
   P->lmax_given = d->lmax_Q;
   P->normG2_given = d->normG2;
+  P->lip_bound = d->lipschitz == DQ_LIP_BOUND;
   dq_status s = DQ_OK;
   auto fail = [&](dq_status st) {
     dq_problem_destroy(P);
     return st;
   };
+  if ((s = flags_clear(ctx)) != DQ_OK) return fail(s);
   const size_t e = P->esz;
   if (d->memory == DQ_DEVICE) {
     P->Q = (void*)d->Q;
@@ -420,9 +560,11 @@ dq_status dq_problem_create(dq_context* ctx, const dq_problem_desc* d, dq_proble
     if ((s = dalloc(&P->GT, p * n * e)) != DQ_OK) return fail(s);
     dim3 blk(32, 8), grd((unsigned)((n + 31) / 32), (unsigned)((p + 31) / 32));
     if (e == 8)
-      k_transpose<double><<<grd, blk, 0, ctx->stream>>>((const double*)P->G, (double*)P->GT, (int)p, (int)n);
+      k_transpose<double><<<grd, blk, 0, ctx->stream>>>((const double*)P->G, (double*)P->GT, (int)p, (int)n,
+                                                         (CheckFlags*)ctx->dflags);
     else
-      k_transpose<float><<<grd, blk, 0, ctx->stream>>>((const float*)P->G, (float*)P->GT, (int)p, (int)n);
+      k_transpose<float><<<grd, blk, 0, ctx->stream>>>((const float*)P->G, (float*)P->GT, (int)p, (int)n,
+                                                        (CheckFlags*)ctx->dflags);
     ++ctx->launches;
     if (cudaGetLastError() != cudaSuccess) {
       set_error("transpose launch failed");
@@ -439,11 +581,29 @@ dq_status dq_problem_create(dq_context* ctx, const dq_problem_desc* d, dq_proble
   if ((s = upload(P, P->ub, d->ub, n, d->memory)) != DQ_OK) return fail(s);
   if ((s = dalloc(&P->x_state, B * n * e)) != DQ_OK) return fail(s);
   if ((s = dalloc(&P->lam_state, std::max<size_t>(B * p, 1) * e)) != DQ_OK) return fail(s);
+  {  // lb <= ub and the symmetry of Q on the device (finiteness: checked by the copies above)
+    CheckFlags* fl = (CheckFlags*)ctx->dflags;
+    const unsigned gb = (unsigned)std::min<size_t>((n + 255) / 256, 1024);
+    const dim3 blk(32, 8), grd((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+    if (e == 8) {
+      k_check_box<double><<<gb, 256, 0, ctx->stream>>>((const double*)P->lb, (const double*)P->ub, (int)n, fl);
+      k_check_sym<double><<<grd, blk, 0, ctx->stream>>>((const double*)P->Q, (int)n, kSymTol64, fl);
+    } else {
+      k_check_box<float><<<gb, 256, 0, ctx->stream>>>((const float*)P->lb, (const float*)P->ub, (int)n, fl);
+      k_check_sym<float><<<grd, blk, 0, ctx->stream>>>((const float*)P->Q, (int)n, kSymTol32, fl);
+    }
+    ctx->launches += 2;
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("validation launch failed");
+      return fail(DQ_ERR_CUDA);
+    }
+  }
   cudaError_t ce = cudaStreamSynchronize(ctx->stream);
   if (ce != cudaSuccess) {
     set_error("problem upload: %s", cudaGetErrorString(ce));
     return fail(DQ_ERR_CUDA);
   }
+  if ((s = flags_check(ctx)) != DQ_OK) return fail(s);
   *out = P;
   return DQ_OK;
 }
@@ -458,18 +618,22 @@ dq_status dq_problem_set_vectors(dq_problem* P, const void* q, const void* g, in
     return DQ_ERR_INVALID;
   }
   std::lock_guard<std::mutex> lk(P->mu);
-  const size_t B = P->batch;
-  if (memory == DQ_HOST) {
-    if ((q && !host_all_finite((const double*)q, B * P->n)) ||
-        (g && P->p && !host_all_finite((const double*)g, B * P->p))) {
-      set_error("non-finite value in q or g");
-      return DQ_ERR_INVALID;
-    }
-  }
-  dq_status s;
-  if (q && (s = upload(P, P->q, q, B * P->n, memory)) != DQ_OK) return s;
-  if (g && P->p && (s = upload(P, P->g, g, B * P->p, memory)) != DQ_OK) return s;
-  DQ_CK(cudaStreamSynchronize(P->ctx->stream));
+  dq_context* ctx = P->ctx;
+  const size_t B = P->batch, bq = q ? B * P->n : 0, bg = (g && P->p) ? B * P->p : 0;
+  // new vectors land in the context's scratch first and replace the handle's
+  // only once they passed the finiteness check
+  void* tmp = nullptr;
+  dq_status s = ctx_scratch(ctx, (bq + bg) * P->esz + 256, &tmp);
+  if (s != DQ_OK) return s;
+  char* tq = (char*)tmp;
+  char* tg = tq + ((bq * P->esz + 255) & ~size_t(255));
+  if ((s = flags_clear(ctx)) != DQ_OK) return s;
+  if (bq && (s = upload(P, tq, q, bq, memory)) != DQ_OK) return s;
+  if (bg && (s = upload(P, tg, g, bg, memory)) != DQ_OK) return s;
+  if ((s = flags_check(ctx)) != DQ_OK) return s;
+  if (bq) DQ_CK(cudaMemcpyAsync(P->q, tq, bq * P->esz, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (bg) DQ_CK(cudaMemcpyAsync(P->g, tg, bg * P->esz, cudaMemcpyDeviceToDevice, ctx->stream));
+  DQ_CK(cudaStreamSynchronize(ctx->stream));
   return DQ_OK;
 }
 

@@ -32,7 +32,8 @@ struct CtaInst {
   int n, p, cone, alg;
   const T *Q, *G, *GT;            // device matrices
   const T *q, *g, *lb, *ub;       // device vectors
-  double lmax_Q, lmin_Q, normG2;  // NaN lmax_Q / normG2: power iteration on chip
+  double lmax_Q, lmin_Q, normG2;  // NaN lmax_Q / normG2: Lanczos estimate (or bound) on chip
+  int lip_bound;                  // 1: guaranteed bounds instead of the Lanczos estimate
   double rho;                     // NaN: 0 for DGM/DFGM, 1/||G||^2 for ADGM/ADFGM
   double LL, sigma, Ld;           // NaN: derived (Sec. 3 Step 1, eq. Ld)
   int inner_fixed, inner_check_every, max_inner;
@@ -395,81 +396,107 @@ __device__ EvalOut cta_eval(const CtaInst<T>& I, CtaWs<T>& W, const T* u, const 
   return e;
 }
 
-// lambda_max of Q (which = 0) or of G'G (which = 1, i.e. ||G||^2) by power
-// iteration from the normalised all-ones vector.  Products in T, norms and
-// the Rayleigh quotient theta in FP64.  Returns theta + ||A v - theta v||, an
-// upper estimate once v lies in the top eigenspace; stops when the residual
-// is below rtol * theta or after max_it steps.
-// Largest eigenvalue theta of the m x m symmetric tridiagonal matrix with
-// diagonal a and off-diagonal b (b[i] joins rows i and i+1), and |s_m|, the
-// last component of its unit eigenvector.  Run by warp 0 in FP32 (FP64 runs
-// at a small fraction of the FP32 rate on this GPU): multisection on Sturm
-// counts, 32 points per round, then the three-term eigenvector recurrence
-// (rescaled) on lane 0.  af, bf: m-float scratch.  Results in out[0], out[1].
-__device__ inline void warp_tridiag_top(const double* a, const double* b, int m, float* af, float* bf,
-                                        double* out) {
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal a and off-diagonal b (b[i] joins rows i and i+1): the count of
+// negative pivots of T - x I = L D L' (Sturm sequence), in precision R.
+template <typename R>
+__device__ __forceinline__ int tri_count_below(const double* a, const double* b, int m, R x) {
+  int cnt = 0;
+  R d = R(1);
+  for (int i = 0; i < m; ++i) {
+    const R bb = i > 0 ? R(b[i - 1]) : R(0);
+    d = (R(a[i]) - x) - (i > 0 ? bb * bb / d : R(0));
+    if (d == R(0)) d = R(-1e-30);
+    cnt += d < R(0);
+  }
+  return cnt;
+}
+
+// One round of 33-way multisection of [lo, hi] (which holds the largest
+// eigenvalue) by the 32 lanes of a warp: lane l tests lo + (hi - lo)(l + 1)/33.
+template <typename R>
+__device__ __forceinline__ void tri_multisect(const double* a, const double* b, int m, R& lo, R& hi) {
   const int lane = threadIdx.x & 31;
-  float lo = INFINITY, hi = -INFINITY;
+  const R x = lo + (hi - lo) * (R(lane + 1) / R(33));
+  const unsigned ball = __ballot_sync(0xffffffffu, tri_count_below<R>(a, b, m, x) == m);  // x above all
+  const int first = ball ? __ffs(ball) - 1 : 32;
+  const R nhi = first < 32 ? __shfl_sync(0xffffffffu, x, first) : hi;
+  const R nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0) : lo;
+  lo = nlo;
+  hi = nhi;
+}
+
+// Largest eigenvalue theta of the m x m symmetric tridiagonal matrix (a, b)
+// and |s_m|, the last component of its unit eigenvector, in FP64 (warp 0):
+// multisection on Sturm counts, first in FP32 to a bracket of relative width
+// 1e-6 (FP64 runs at a small fraction of the FP32 rate on this GPU), then in
+// FP64 from that bracket widened by 1e-5 (checked by two FP64 Sturm counts;
+// the Gershgorin interval when the check fails) to 1e-13; then the
+// three-term eigenvector recurrence (rescaled) in FP64 on lane 0.  Results in
+// out[0], out[1].
+__device__ inline void warp_tridiag_top(const double* a, const double* b, int m, double* out) {
+  const int lane = threadIdx.x & 31;
+  double glo = INFINITY, ghi = -INFINITY;
   for (int i = lane; i < m; i += 32) {
-    af[i] = float(a[i]);
-    bf[i] = i + 1 < m ? float(b[i]) : 0.f;
-    const float r = float((i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0));
-    lo = fminf(lo, af[i] - r);
-    hi = fmaxf(hi, af[i] + r);
+    const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
+    glo = fmin(glo, a[i] - r);
+    ghi = fmax(ghi, a[i] + r);
   }
   for (int o = 16; o > 0; o >>= 1) {
-    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
   }
-  __syncwarp();
+  float flo = float(glo), fhi = float(ghi);
   for (int round = 0; round < 8; ++round) {
-    const float x = lo + (hi - lo) * (float(lane + 1) / 33.f);
-    int cnt = 0;
-    float d = 1.f;
-    for (int i = 0; i < m; ++i) {
-      d = (af[i] - x) - (i > 0 ? bf[i - 1] * bf[i - 1] / d : 0.f);
-      if (d == 0.f) d = -1e-30f;
-      cnt += d < 0.f;
+    tri_multisect<float>(a, b, m, flo, fhi);
+    if (fhi - flo <= 1e-6f * fmaxf(fabsf(flo), fabsf(fhi))) break;
+  }
+  const double sc = fmax(fabs(double(flo)), fabs(double(fhi)));
+  double lo = double(flo) - 1e-5 * sc - 1e-300, hi = double(fhi) + 1e-5 * sc + 1e-300;
+  {  // lane 0: some eigenvalue is >= lo; lane 1: every eigenvalue is < hi
+    const int c = tri_count_below<double>(a, b, m, lane == 0 ? lo : hi);
+    const bool okl = __shfl_sync(0xffffffffu, c, 0) < m, okh = __shfl_sync(0xffffffffu, c, 1) == m;
+    if (!(okl && okh)) {
+      lo = glo;
+      hi = ghi;
     }
-    const unsigned ball = __ballot_sync(0xffffffffu, cnt == m);  // x above every eigenvalue
-    const int first = ball ? __ffs(ball) - 1 : 32;
-    const float nhi = first < 32 ? __shfl_sync(0xffffffffu, x, first) : hi;
-    const float nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0) : lo;
-    lo = nlo;
-    hi = nhi;
-    if (hi - lo <= 1e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
+  }
+  for (int round = 0; round < 14; ++round) {
+    if (hi - lo <= 1e-13 * fmax(fabs(lo), fabs(hi))) break;
+    tri_multisect<double>(a, b, m, lo, hi);
   }
   if (lane == 0) {
-    float up = 0.f, u = 1.f, nrm2 = 1.f;
+    double up = 0.0, u = 1.0, nrm2 = 1.0;
     for (int i = 0; i + 1 < m; ++i) {
-      if (bf[i] == 0.f) {
-        up = 0.f; u = 1.f; nrm2 = 1.f;
+      if (b[i] == 0.0) {  // the matrix splits: the leading block's vector ends here
+        up = 0.0; u = 1.0; nrm2 = 1.0;
         continue;
       }
-      const float un = ((hi - af[i]) * u - (i > 0 ? bf[i - 1] * up : 0.f)) / bf[i];
+      const double un = ((hi - a[i]) * u - (i > 0 ? b[i - 1] * up : 0.0)) / b[i];
       up = u;
       u = un;
       nrm2 += u * u;
-      if (nrm2 > 1e30f) {
-        const float sc = rsqrtf(nrm2);
-        up *= sc; u *= sc; nrm2 = 1.f;
+      if (nrm2 > 1e200) {
+        const double s = 1.0 / sqrt(nrm2);
+        up *= s; u *= s; nrm2 = 1.0;
       }
     }
     out[0] = hi;
-    out[1] = fabsf(u) * rsqrtf(nrm2);
+    out[1] = fabs(u) / sqrt(nrm2);
   }
+  __syncwarp();
 }
 
 // lambda_max of Q (which = 0) or G'G (which = 1) by the Lanczos method
-// without reorthogonalisation (only the extreme Ritz value is used).  After
-// step j the largest Ritz value theta of T_j and its residual r = beta_j |s_j|
-// (there is an eigenvalue within r of theta) give the estimate theta + 2 r,
-// accepted once r <= rtol * theta; the factor 2 covers most starts whose
-// component along the top eigenvector is small (Lanczos then settles first on
-// the next eigenvalue).  A 1e-5 relative margin covers the FP32 tridiagonal
-// solve.  Scratch: A.x, B.x, A.Qx, A.Gx, A.xp, A.xn, dn, usum.
+// without reorthogonalisation (only the extreme Ritz value is used), from the
+// SplitMix64 start vector, for lz_min_steps(n) steps (at most kLzMaxSteps;
+// all n when n is smaller, the exhausted case): the top Ritz value theta of
+// T_k and its residual r = beta_k |s_k| give lz_estimate (theta / (1 - eps)
+// or theta + 2 r, whichever is larger).  Products in T, the three-term
+// recurrence and the tridiagonal eigenproblem in FP64.
+// Scratch: A.x, B.x, A.Qx, A.Gx, dn, usum.
 template <typename T>
-__device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int max_it, int which, double rtol) {
+__device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int which) {
   const int n = I.n, p = I.p;
   T* v = W.A.x;
   T* vp = W.B.x;
@@ -477,15 +504,21 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int max_it, int 
   T* t = W.A.Gx;
   double* al = W.dn;
   double* be = W.usum;
-  const T v0 = T(1.0 / sqrt(double(n)));
+  double ps = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    v[i] = v0;
+    const double s = lz_start((unsigned long long)i);
+    ps += s * s;
+  }
+  const double inv = 1.0 / sqrt(block_sum(ps, W.red));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    v[i] = T(lz_start((unsigned long long)i) * inv);
     vp[i] = T(0);
   }
   __syncthreads();
-  const int mmax = min(n, max_it);
+  const int ksteps = min(lz_min_steps(n), kLzMaxSteps);
   double theta = 0.0, r = 0.0, beta_prev = 0.0;
-  for (int j = 0; j < mmax; ++j) {
+  bool exhausted = false;
+  for (int j = 0; j < ksteps; ++j) {
     if (which == 0) {
       mtv<T>(W.Q, n, n, n, v, w, W.part);
     } else {
@@ -508,18 +541,15 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int max_it, int 
       al[j] = alpha;
       be[j] = beta;
     }
-    const bool last = j + 1 == mmax || !(beta > 1e-300);
-    if (last || (j >= 3 && ((j + 1) % 4 == 0))) {
+    const bool invariant = !(beta > 1e-300);
+    if (invariant || j + 1 == ksteps) {
       __syncthreads();
-      if (threadIdx.x < 32) warp_tridiag_top(al, be, j + 1, (float*)W.A.xp, (float*)W.A.xn, W.red + 34);
+      if (threadIdx.x < 32) warp_tridiag_top(al, be, j + 1, W.red + 34);
       __syncthreads();
       theta = W.red[34];
       r = beta * W.red[35];
-      if (!(beta > 1e-300) || j + 1 == n) {  // invariant subspace: theta is exact up to rounding
-        r = 0.0;
-        break;
-      }
-      if (r <= rtol * theta) break;
+      exhausted = invariant || j + 1 == n;
+      break;
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       vp[i] = v[i];
@@ -529,7 +559,48 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int max_it, int 
     __syncthreads();
   }
   __syncthreads();
-  return theta + 2.0 * r + 1e-5 * fabs(theta);
+  return lz_estimate(theta, r, exhausted, sizeof(T) == 8 ? 1.2e-16 : 6.0e-8);
+}
+
+// Guaranteed upper bounds (no estimate): lambda_max(Q) <= min(max_i sum_j |Q_ij|
+// (Gershgorin), ||Q||_F) and ||G||^2 <= min(||G||_1 ||G||_inf, ||G||_F^2), from
+// FP64 column sums (Q symmetric: column sums are row sums; GT's column sums
+// are G's row sums).
+template <typename T>
+__device__ double cta_col_abs_max(const T* M, int rows, int cols, double* red, double* fro) {
+  double mx = 0.0, f = 0.0;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) {
+      const double v = double(M[(size_t)r * cols + c]);
+      s += fabs(v);
+      f += v * v;
+    }
+    mx = fmax(mx, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  double m = 0.0;
+  for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) m = fmax(m, red[i]);
+  __syncthreads();
+  *fro = block_sum(f, red);
+  return m;
+}
+
+template <typename T>
+__device__ double cta_bound(const CtaInst<T>& I, CtaWs<T>& W, int which) {
+  const int n = I.n, p = I.p;
+  double fro = 0.0;
+  if (which == 0) {
+    const double g = cta_col_abs_max<T>(W.Q, n, n, W.red, &fro);
+    return fmin(g, sqrt(fro));
+  }
+  const double c1 = cta_col_abs_max<T>(W.G, p, n, W.red, &fro);  // ||G||_1
+  double f2 = 0.0;
+  const double ci = cta_col_abs_max<T>(W.GT, n, p, W.red, &f2);  // ||G||_inf
+  return fmin(c1 * ci, fro);
 }
 
 __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -596,8 +667,8 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
   }
   __syncthreads();
   // FP64 constants (a1): lambda_max(Q), ||G||^2, then L_L, sigma_L, L_d, rho
-  if (isnan(I.lmax_Q)) I.lmax_Q = cta_lanczos<T>(I, W, 160, 0, 1e-3);
-  if (isnan(I.normG2)) I.normG2 = p > 0 ? cta_lanczos<T>(I, W, 160, 1, 1e-3) : 0.0;
+  if (isnan(I.lmax_Q)) I.lmax_Q = I.lip_bound ? cta_bound<T>(I, W, 0) : cta_lanczos<T>(I, W, 0);
+  if (isnan(I.normG2)) I.normG2 = p > 0 ? (I.lip_bound ? cta_bound<T>(I, W, 1) : cta_lanczos<T>(I, W, 1)) : 0.0;
   const double lmin = isnan(I.lmin_Q) ? 0.0 : I.lmin_Q;
   if (isnan(I.rho)) I.rho = (I.alg == ALG_ADGM || I.alg == ALG_ADFGM) ? (I.normG2 > 0.0 ? 1.0 / I.normG2 : 1.0) : 0.0;
   if (isnan(I.LL)) I.LL = I.lmax_Q + I.rho * I.normG2;
@@ -641,6 +712,22 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
   }
   __syncthreads();
 
+  // Upper bound of F over the box, F(u) <= sum_i max(q_i lb_i, q_i ub_i) +
+  // lambda_max(Q)/2 sum_i max(lb_i^2, ub_i^2) (twice the lambda_max estimate,
+  // so a low estimate cannot spoil it).  When the certified lower bound d_lb on
+  // F* passes it, no feasible point exists (weak duality): DQ_ERR_DIVERGED.
+  double fub = 0.0;
+  {
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double qi = double(I.q[i]), l = double(I.lb[i]), u = double(I.ub[i]);
+      a += fmax(qi * l, qi * u);
+      b += fmax(l * l, u * u);
+    }
+    const double sa = block_sum(a, W.red), sb = block_sum(b, W.red);
+    fub = sa + I.lmax_Q * sb;
+    fub += 1e-9 * (fabs(fub) + 1.0);
+  }
   const bool aug = I.rho > 0.0, fast = alg_fast(I.alg);
   const T alpha = T(1.0 / (2.0 * I.Ld));
   const T rho = T(I.rho);
@@ -723,6 +810,9 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
       if ((I.want_last && !(isfinite(f_last) && isfinite(i_last))) ||
           (I.want_avg && !(isfinite(f_avg) && isfinite(i_avg)))) {
         status = ST_NONFINITE;
+        done = true;
+      } else if (d_lb > fub) {  // infeasible: the dual lower bound passed max_U F
+        status = ST_DIVERGED;
         done = true;
       }
       if (I.outer_fixed <= 0 && !done) {

@@ -137,6 +137,7 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
       I.lmax_Q = c.fresh ? P->lmax_given : P->lmax_Q;
       I.lmin_Q = lmin;
       I.normG2 = c.fresh ? P->normG2_given : P->normG2;
+      I.lip_bound = P->lip_bound;
       I.rho = c.rho;
       I.LL = c.LL;
       I.sigma = c.sigma;
@@ -260,6 +261,9 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
       fill_result(&results[k], h_res[k], &h_con[6 * k], cfgs[i]);
       const dq_status st_i = (dq_status)h_res[k].status;
       if (st_i == DQ_ERR_INVALID) set_error("instance %zu: invalid constants (DGM/DFGM need lmin_Q > 0)", k);
+      if (st_i == DQ_ERR_DIVERGED)
+        set_error("instance %zu: infeasible (the certified dual lower bound passed the largest value of F on the box)",
+                  k);
       if (st_i < 0 || worst < 0) worst = (st_i < worst) ? st_i : worst;
       else if (st_i > worst) worst = st_i;
       if (o && o->memory == DQ_HOST && st_i >= 0) {

@@ -98,4 +98,45 @@ template <typename T> struct AccurateAcc;
 template <> struct AccurateAcc<double> { using type = Acc64; };
 template <> struct AccurateAcc<float> { using type = Dot2f; };
 
+// ---- Lanczos estimates of lambda_max(Q) and ||G||^2 = lambda_max(G'G) ------
+//
+// Entry i of the start vector: a value in [-1, 1) from the SplitMix64
+// generator (Steele, Lea and Flood, OOPSLA 2014) at counter i.  A pseudo-random
+// start has a component along the top eigenvector whatever structure Q has
+// (an all-ones start is orthogonal to, e.g., a top eigenvector (1, -1, 0, ...)).
+__host__ __device__ inline double lz_start(unsigned long long i) {
+  unsigned long long z = 0x2545F4914F6CDD1DULL + (i + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return double(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// Relative margin eps and failure probability delta of the estimate.  For a
+// start vector drawn uniformly from the sphere, the top Ritz value theta_k of
+// k Lanczos steps satisfies P(theta_k < (1 - eps) lambda_max) <=
+// 1.648 sqrt(n) exp(-sqrt(eps) (2k - 1)) (Kuczynski and Wozniakowski, SIAM J.
+// Matrix Anal. Appl. 13(4), 1992).  After lz_min_steps(n) steps that is at
+// most delta, so theta_k / (1 - eps) is an upper bound of lambda_max with
+// probability >= 1 - delta (the SplitMix64 start stands in for the random one).
+static constexpr double kLzEps = 0.01, kLzDelta = 1e-3;
+static constexpr int kLzMaxSteps = 160;
+
+__host__ __device__ inline int lz_min_steps(int n) {
+  const double k = 0.5 * (log(1.648 * sqrt(double(n)) / kLzDelta) / sqrt(kLzEps) + 1.0);
+  const int kk = int(ceil(k));
+  return kk < n ? kk : n;
+}
+
+// The returned estimate: theta + 2 r (r = beta_k |s_k| is the residual of the
+// Ritz pair, so an eigenvalue lies within r of theta) and at least
+// theta / (1 - eps).  After n steps (or an invariant subspace, beta = 0) the
+// Krylov space holds the top eigenvector and theta is exact up to the
+// rounding `ulp_rel` of the products.
+__host__ __device__ inline double lz_estimate(double theta, double r, bool exhausted, double ulp_rel) {
+  if (exhausted) return theta + 2.0 * r + 64.0 * ulp_rel * fabs(theta);
+  const double a = theta + 2.0 * r, b = theta / (1.0 - kLzEps);
+  return a > b ? a : b;
+}
+
 }  // namespace dq

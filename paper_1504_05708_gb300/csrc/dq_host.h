@@ -35,6 +35,14 @@ struct GridWs;   // large-instance engine workspace (grid_engine.cu)
 struct TcWs;     // tensor-core batch workspace (tc_engine.cu)
 struct ServeState;
 
+// Validation results of the problem-data checks on the device (dq_problem_create).
+struct CheckFlags {
+  int nonfinite;        // a NaN or Inf in Q, q, G, g, lb or ub
+  int bad_box;          // lb_i > ub_i somewhere
+  int asym;             // a pair |Q_ij - Q_ji| > tol sqrt(|Q_ii Q_jj|)
+  int asym_i, asym_j;   // one such pair
+};
+
 // Resolved solve options (defaults applied; NaN kept where the device derives).
 struct SolveCfg {
   int alg, output, inner_stop, engine;
@@ -72,6 +80,15 @@ struct dq_context {
   uint64_t gkey = 0;
   // autotuned CTA-engine configurations: size-histogram signature -> (threads, smem cap)
   std::map<std::string, std::pair<int, int>> tuned;
+  // host -> device upload: a grow-only device staging buffer (two halves that
+  // alternate), a copy stream that overlaps the copies with the conversion
+  // kernels on `stream`, and the validation flags the device kernels set
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t cev[4] = {nullptr, nullptr, nullptr, nullptr};
+  int* dflags = nullptr;   // device dq::CheckFlags
+  int* hflags = nullptr;   // pinned mirror
   // lifetime: problems keep their context alive; a destroy requested while
   // problems exist is carried out when the last one is destroyed
   int live_problems = 0;
@@ -89,6 +106,7 @@ struct dq_problem {
   bool has_state = false;
   double lmax_Q = NAN, lmin_Q = NAN, normG2 = NAN;
   double lmax_given = NAN, normG2_given = NAN;  // as passed in dq_problem_desc
+  int lip_bound = 0;                            // dq_problem_desc.lipschitz == DQ_LIP_BOUND
   dq::GridWs* gws = nullptr;
   dq::TcWs* tws = nullptr;
   std::mutex mu;

@@ -62,7 +62,7 @@ struct Ctrl {          // device control block of the grid engine
   unsigned int arrive; // last-block counter of the reductions
   int wait_err;        // set when a bounded wait of the single-pass kernel gave up
   double cert;
-  double sums[8];      // results of the reduction kernels
+  double sums[10];     // results of the reduction kernels
 };
 
 enum { VM_COPY = 0, VM_STEP = 1, VM_W = 2, VM_COPY2 = 3 };
@@ -257,6 +257,24 @@ __global__ void __launch_bounds__(512) k_cert(const T* x, const T* Qx, const T* 
   }
 }
 
+// Parts of the upper bound of F over the box: sum_i max(q_i lb_i, q_i ub_i)
+// and sum_i max(lb_i^2, ub_i^2) into ctrl->sums[7], sums[8].
+template <typename T>
+__global__ void __launch_bounds__(512) k_fub(const T* q, const T* lb, const T* ub, int n, double* partials,
+                                             Ctrl* ctrl) {
+  double part[2] = {0.0, 0.0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double qi = double(q[i]), l = double(lb[i]), u = double(ub[i]);
+    part[0] += fmax(qi * l, qi * u);
+    part[1] += fmax(l * l, u * u);
+  }
+  double out[2];
+  if (grid_reduce<2>(part, partials, ctrl, out) && threadIdx.x == 0) {
+    ctrl->sums[7] = out[0];
+    ctrl->sums[8] = out[1];
+  }
+}
+
 // Dual step of Algorithm DFOM and the running average of eq. average_primal.
 template <typename T>
 __global__ void k_dual(const T* Gx, const T* g, const T* mu, T* lam, int p, T alpha, T rho, int cone,
@@ -376,11 +394,14 @@ __global__ void __launch_bounds__(512) k_vw(const T* v, const T* w, int n, doubl
 }
 
 // Lanczos three-term step on the device: w -= alpha v + beta_prev v_prev with
-// alpha = v.w from k_vw (ctrl->sums[4]), and ||w||^2 into ctrl->sums[6].
+// alpha = v.w from k_vw (ctrl->sums[4]) and beta_prev = rec[2 j - 1]; ||w||^2
+// into ctrl->sums[6]; the last block records alpha_j and beta_j in rec[2 j],
+// rec[2 j + 1], so the whole run needs no host round trip.
 template <typename T>
-__global__ void __launch_bounds__(512) k_lz_update(const T* v, const T* vp, T* w, int n, double beta_prev,
-                                                   double* partials, Ctrl* ctrl) {
+__global__ void __launch_bounds__(512) k_lz_update(const T* v, const T* vp, T* w, int n, const double* rec, int j,
+                                                   double* rec_out, double* partials, Ctrl* ctrl) {
   const double alpha = ctrl->sums[4];
+  const double beta_prev = j > 0 ? rec[2 * j - 1] : 0.0;
   double part[1] = {0.0};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double r = double(w[i]) - alpha * double(v[i]) - beta_prev * double(vp[i]);
@@ -388,23 +409,59 @@ __global__ void __launch_bounds__(512) k_lz_update(const T* v, const T* vp, T* w
     part[0] += r * r;
   }
   double out[1];
-  if (grid_reduce<1>(part, partials, ctrl, out) && threadIdx.x == 0) ctrl->sums[6] = out[0];
+  if (grid_reduce<1>(part, partials, ctrl, out) && threadIdx.x == 0) {
+    ctrl->sums[6] = out[0];
+    rec_out[2 * j] = alpha;
+    rec_out[2 * j + 1] = sqrt(out[0]);
+  }
 }
 
-// v_prev = v, v = w / beta (beta = sqrt(ctrl->sums[6])); init: v = 1/sqrt(n), v_prev = 0.
+// v_prev = v, v = w / beta (beta = sqrt(ctrl->sums[6]); beta = 0 leaves v = 0,
+// which ends the Krylov space); init: v = the SplitMix64 start vector times
+// `scale` (its inverse norm), v_prev = 0.
 template <typename T>
-__global__ void k_lz_next(T* v, T* vp, const T* w, int n, const Ctrl* ctrl, int init) {
-  const double nb = ctrl->sums[6];
+__global__ void k_lz_next(T* v, T* vp, const T* w, int n, const Ctrl* ctrl, int init, double scale) {
+  const double nb = init ? 0.0 : ctrl->sums[6];
   const double inv = nb > 0.0 ? 1.0 / sqrt(nb) : 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (init) {
-      v[i] = T(1.0 / sqrt(double(n)));
+      v[i] = T(lz_start((unsigned long long)i) * scale);
       vp[i] = T(0);
     } else {
       vp[i] = v[i];
       v[i] = T(double(w[i]) * inv);
     }
   }
+}
+
+// Column sums of |M| and of M^2 over row segment blockIdx.y of an rows x cols
+// row-major matrix (guaranteed bounds of the spectral constants).
+template <typename T>
+__global__ void k_colabs(const T* M, int rows, int cols, int segs, double* abs_part, double* sq_part) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  const int r0 = (int)((long long)rows * blockIdx.y / segs), r1 = (int)((long long)rows * (blockIdx.y + 1) / segs);
+  double a = 0.0, q = 0.0;
+  for (int r = r0; r < r1; ++r) {
+    const double v = double(M[(size_t)r * cols + c]);
+    a += fabs(v);
+    q += v * v;
+  }
+  abs_part[(size_t)blockIdx.y * cols + c] = a;
+  sq_part[(size_t)blockIdx.y * cols + c] = q;
+}
+
+template <typename T>
+__global__ void k_colabs_sum(int cols, int segs, double* abs_part, double* sq_part) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double a = 0.0, q = 0.0;
+  for (int g = 0; g < segs; ++g) {
+    a += abs_part[(size_t)g * cols + c];
+    q += sq_part[(size_t)g * cols + c];
+  }
+  abs_part[c] = a;
+  sq_part[c] = q;
 }
 
 // H = Q + rho G'G for the equality-constrained augmented Lagrangian (K = {0}:
@@ -545,6 +602,7 @@ struct GridWs {
   void *X[3], *QX[3], *GX[3], *XB[3], *QXB[3], *GXB[3];
   void *c, *tn, *w, *whi, *wlo, *mu, *lam, *lamp, *ul, *uavg, *pv, *pw, *pt;
   double *usum, *dQ, *dG, *gwh, *gwl;
+  double* lzrec = nullptr;  // alpha_j, beta_j of the Lanczos runs (2 kLzMaxSteps)
   int blocks = 0;
   // single-pass (v2) layout: packed upper triangle of Q and partial sums
   void* v2mem = nullptr;
@@ -570,6 +628,7 @@ void grid_free(GridWs* w) {
   if (w->ctrl) cudaFree(w->ctrl);
   if (w->hctrl) cudaFreeHost(w->hctrl);
   if (w->partials) cudaFree(w->partials);
+  if (w->lzrec) cudaFree(w->lzrec);
   if (w->v2mem) cudaFree(w->v2mem);
   if (w->H) cudaFree(w->H);
   if (w->zp) cudaFree(w->zp);
@@ -615,6 +674,7 @@ static dq_status grid_ws(dq_problem* P, GridWs** out) {
   W->dG = (double*)take(dp);
   W->blocks = P->ctx->num_sms * 2;
   if (cudaMalloc(&W->ctrl, sizeof(Ctrl)) != cudaSuccess || cudaMallocHost(&W->hctrl, 2 * sizeof(Ctrl)) != cudaSuccess ||
+      cudaMalloc(&W->lzrec, sizeof(double) * 2 * kLzMaxSteps) != cudaSuccess ||
       cudaMalloc(&W->partials, sizeof(double) * 8 * 4096) != cudaSuccess ||
       cudaEventCreateWithFlags(&W->ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&W->ev[1], cudaEventDisableTiming) != cudaSuccess) {
@@ -684,25 +744,27 @@ struct GridRun {
   }
 
   // lambda_max of Q (which = 0) or G'G (which = 1) by the Lanczos method
-  // (no reorthogonalisation: only the extreme Ritz value is used): after step
-  // j the largest Ritz value theta of the tridiagonal T_j and its residual
-  // r = beta_j |s_j| (there is an eigenvalue within r of theta) give the
-  // estimate theta + 2 r, accepted once r <= 1e-3 theta; the factor 2 covers
-  // most starts with a small component along the top eigenvector.  Matrix
-  // products run on the device; the tridiagonal problem (at most 200 x 200)
-  // on the host.
+  // (no reorthogonalisation: only the extreme Ritz value is used) from the
+  // SplitMix64 start vector for lz_min_steps(n) steps (all n when n is
+  // smaller): matrix products and the three-term recurrence on the device with
+  // alpha_j, beta_j recorded there, one copy to the host at the end, the
+  // tridiagonal eigenproblem on the host in FP64, and lz_estimate of the top
+  // Ritz value theta and its residual (at least theta / (1 - eps)).
   dq_status power(int which, double* out) {
     T* vv = v(W->pv);
     T* ww = v(W->pw);
     T* tt = v(W->pt);
     T* vp = v(W->XB[0]);  // scratch here: the last-iterate chain is idle during constants
     const int eb = std::min(blocks, 4096);
-    k_lz_next<T><<<eb, 256, 0, st>>>(vv, vp, ww, n, W->ctrl, 1);
+    double ss = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double z = lz_start((unsigned long long)i);
+      ss += z * z;
+    }
+    k_lz_next<T><<<eb, 256, 0, st>>>(vv, vp, ww, n, W->ctrl, 1, 1.0 / sqrt(ss));
     ++P->ctx->launches;
-    std::vector<double> al, be;
-    double theta = 0.0, r = 0.0, beta_prev = 0.0;
-    const int mmax = std::min(n, 200);
-    for (int j = 0; j < mmax; ++j) {
+    const int ksteps = std::min(lz_min_steps(n), kLzMaxSteps);
+    for (int j = 0; j < ksteps; ++j) {
       cudaError_t e;
       if (which == 0) {
         e = gemv(Q(), n, nullptr, 0, n, vv, ww, nullptr);
@@ -715,27 +777,71 @@ struct GridRun {
         return DQ_ERR_CUDA;
       }
       k_vw<T><<<eb, 512, 0, st>>>(vv, ww, n, W->partials, W->ctrl);
-      k_lz_update<T><<<eb, 512, 0, st>>>(vv, vp, ww, n, beta_prev, W->partials, W->ctrl);
+      k_lz_update<T><<<eb, 512, 0, st>>>(vv, vp, ww, n, W->lzrec, j, W->lzrec, W->partials, W->ctrl);
       P->ctx->launches += 2;
-      DQ_CK(cudaMemcpyAsync(W->hctrl, W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-      DQ_CK(cudaStreamSynchronize(st));
-      const double alpha = W->hctrl->sums[4], beta = sqrt(std::max(W->hctrl->sums[6], 0.0));
-      al.push_back(alpha);
-      be.push_back(beta);
-      double sl = 0.0;
-      tridiag_top(al, be, j + 1, &theta, &sl);
-      r = beta * sl;
-      if (!(beta > 1e-300) || j + 1 == n) {  // invariant subspace: theta is exact
-        r = 0.0;
-        break;
+      if (j + 1 < ksteps) {
+        k_lz_next<T><<<eb, 256, 0, st>>>(vv, vp, ww, n, W->ctrl, 0, 0.0);
+        ++P->ctx->launches;
       }
-      if (j >= 2 && r <= 1e-3 * theta) break;
-      k_lz_next<T><<<eb, 256, 0, st>>>(vv, vp, ww, n, W->ctrl, 0);
-      ++P->ctx->launches;
       DQ_CK(cudaGetLastError());
-      beta_prev = beta;
     }
-    *out = theta + 2.0 * r + 1e-12 * fabs(theta);
+    std::vector<double> rec(2 * (size_t)ksteps);
+    DQ_CK(cudaMemcpyAsync(rec.data(), W->lzrec, rec.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    DQ_CK(cudaStreamSynchronize(st));
+    std::vector<double> al, be;
+    bool invariant = false;
+    for (int j = 0; j < ksteps && !invariant; ++j) {
+      al.push_back(rec[2 * j]);
+      be.push_back(rec[2 * j + 1]);
+      invariant = !(rec[2 * j + 1] > 1e-300);
+    }
+    const int m = (int)al.size();
+    double theta = 0.0, sl = 0.0;
+    tridiag_top(al, be, m, &theta, &sl);
+    const double r = be[m - 1] * sl;
+    *out = lz_estimate(theta, r, invariant || m == n, sizeof(T) == 8 ? 1.2e-16 : 6.0e-8);
+    return DQ_OK;
+  }
+
+  // Guaranteed upper bounds (no estimate): lambda_max(Q) <= min(max_i sum_j
+  // |Q_ij| (Gershgorin), ||Q||_F) and ||G||^2 <= min(||G||_1 ||G||_inf,
+  // ||G||_F^2), from FP64 column sums on the device (Q symmetric: column sums
+  // are row sums; G' has G's row sums as its column sums).
+  dq_status bound(int which, double* out) {
+    auto colmax = [&](const T* M, int rows, int cols, double* mx, double* fro) -> dq_status {
+      const int segs = 32;
+      void* buf = nullptr;
+      dq_status s = ctx_scratch(P->ctx, 2 * (size_t)segs * cols * sizeof(double), &buf);
+      if (s != DQ_OK) return s;
+      double* ab = (double*)buf;
+      double* sq = ab + (size_t)segs * cols;
+      k_colabs<T><<<dim3((cols + 255) / 256, segs), 256, 0, st>>>(M, rows, cols, segs, ab, sq);
+      k_colabs_sum<T><<<(cols + 255) / 256, 256, 0, st>>>(cols, segs, ab, sq);
+      P->ctx->launches += 2;
+      DQ_CK(cudaGetLastError());
+      std::vector<double> h(2 * (size_t)cols);
+      DQ_CK(cudaMemcpyAsync(h.data(), ab, cols * sizeof(double), cudaMemcpyDeviceToHost, st));
+      DQ_CK(cudaMemcpyAsync(h.data() + cols, sq, cols * sizeof(double), cudaMemcpyDeviceToHost, st));
+      DQ_CK(cudaStreamSynchronize(st));
+      double m = 0.0, f = 0.0;
+      for (int c = 0; c < cols; ++c) {
+        m = std::max(m, h[c]);
+        f += h[cols + c];
+      }
+      *mx = m;
+      *fro = f;
+      return DQ_OK;
+    };
+    double a = 0.0, f = 0.0, b = 0.0, f2 = 0.0;
+    dq_status s;
+    if (which == 0) {
+      if ((s = colmax(Q(), n, n, &a, &f)) != DQ_OK) return s;
+      *out = std::min(a, sqrt(f));
+      return DQ_OK;
+    }
+    if ((s = colmax(G(), p, n, &a, &f)) != DQ_OK) return s;   // ||G||_1, ||G||_F^2
+    if ((s = colmax(GT(), n, p, &b, &f2)) != DQ_OK) return s; // ||G||_inf
+    *out = std::min(a * b, f);
     return DQ_OK;
   }
 
@@ -1173,6 +1279,15 @@ struct GridRun {
     }
     cudaError_t e = gemv(Qm(), n, p > 0 ? G() : nullptr, p, n, v(W->X[0]), v(W->QX[0]), p > 0 ? v(W->GX[0]) : nullptr);
     if (e != cudaSuccess) { set_error("init: %s", cudaGetErrorString(e)); return DQ_ERR_CUDA; }
+    // Upper bound of F over the box (twice the lambda_max estimate): when the
+    // certified lower bound d_lb on F* passes it, no feasible point exists
+    // (weak duality) and the solve returns DQ_ERR_DIVERGED.
+    k_fub<T><<<eb, 512, 0, st>>>(q(), lb(), ub(), n, W->partials, W->ctrl);
+    ++P->ctx->launches;
+    DQ_CK(cudaMemcpyAsync(W->hctrl, W->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    DQ_CK(cudaStreamSynchronize(st));
+    double fub = W->hctrl->sums[7] + P->lmax_Q * W->hctrl->sums[8];
+    fub += 1e-9 * (fabs(fub) + 1.0);
     int cur = 0;
     double theta = 1.0, S = 0.0, d_lb = -INFINITY;
     double f_last = NAN, i_last = NAN, f_avg = NAN, i_avg = NAN;
@@ -1227,6 +1342,9 @@ struct GridRun {
             (want_avg && !(std::isfinite(f_avg) && std::isfinite(i_avg)))) {
           status = ST_NONFINITE;
           done = true;
+        } else if (d_lb > fub) {  // infeasible: the dual lower bound passed max_U F
+          status = ST_DIVERGED;
+          done = true;
         }
         if (cfg->fixed_outer <= 0 && !done) {
           conv_last = want_last && i_last <= cfg->eps_out && f_last - d_lb <= cfg->eps_out;
@@ -1279,6 +1397,8 @@ struct GridRun {
     d.f_last = f_last; d.infeas_last = i_last; d.f_avg = f_avg; d.infeas_avg = i_avg; d.d_lb = d_lb;
     const double consts[6] = {P->lmax_Q, P->normG2, LL, Ld, sigma, rho};
     fill_result(res, d, consts, *cfg);
+    if (d.status == ST_DIVERGED)
+      set_error("infeasible: the certified dual lower bound passed the largest value of F on the box");
     return (dq_status)d.status;
   }
 };
@@ -1289,10 +1409,10 @@ static dq_status constants_T(dq_problem* P, GridWs* W) {
   R.P = P; R.W = W; R.st = P->ctx->stream; R.n = P->n; R.p = P->p; R.cone = P->cone; R.blocks = W->blocks;
   R.cfg = nullptr;
   dq_status s;
-  if (isnan(P->lmax_Q) && (s = R.power(0, &P->lmax_Q)) != DQ_OK) return s;
+  if (isnan(P->lmax_Q) && (s = P->lip_bound ? R.bound(0, &P->lmax_Q) : R.power(0, &P->lmax_Q)) != DQ_OK) return s;
   if (isnan(P->normG2)) {
     if (P->p == 0) P->normG2 = 0.0;
-    else if ((s = R.power(1, &P->normG2)) != DQ_OK) return s;
+    else if ((s = P->lip_bound ? R.bound(1, &P->normG2) : R.power(1, &P->normG2)) != DQ_OK) return s;
   }
   return DQ_OK;
 }

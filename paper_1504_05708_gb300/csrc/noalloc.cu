@@ -32,6 +32,11 @@ static constexpr size_t kOffCounter = 1024;  // work-queue counter (int)
 static constexpr size_t kOffResult = 1280;   // DevResult
 static constexpr size_t kOffConsts = 1536;   // 6 doubles
 static constexpr size_t kOffGT = 4096;       // G' (n x p elements)
+static_assert(sizeof(CtaInst<double>) <= kOffCounter - kOffInst && sizeof(CtaInst<float>) <= kOffCounter - kOffInst,
+              "the instance descriptor overlaps the work-queue counter");
+static_assert(sizeof(int) <= kOffResult - kOffCounter, "the counter overlaps the result");
+static_assert(sizeof(DevResult) <= kOffConsts - kOffResult, "the result overlaps the constants");
+static_assert(6 * sizeof(double) <= kOffGT - kOffConsts, "the constants overlap G'");
 
 // Host-side device address of the scratch, looked up once per device.
 static constexpr int kMaxDevices = 64;
@@ -117,6 +122,7 @@ static dq_status run_noalloc(int device, const dq_problem_desc* d, const SolveCf
   I.lmax_Q = d->lmax_Q;
   I.lmin_Q = d->lmin_Q;
   I.normG2 = d->normG2;
+  I.lip_bound = d->lipschitz == DQ_LIP_BOUND;
   I.rho = c.rho;
   I.LL = c.LL;
   I.sigma = c.sigma;
@@ -168,7 +174,8 @@ extern "C" dq_status dq_solve_noalloc(int device, const dq_problem_desc* desc, c
   }
   if (desc->memory != DQ_DEVICE || desc->batch != 1 || (desc->prec != DQ_FP64 && desc->prec != DQ_FP32) ||
       desc->n < 1 || desc->p < 0 || (out && out->memory != DQ_DEVICE) ||
-      (desc->cone != DQ_CONE_INEQ && desc->cone != DQ_CONE_EQ)) {
+      (desc->cone != DQ_CONE_INEQ && desc->cone != DQ_CONE_EQ) ||
+      (desc->lipschitz != DQ_LIP_LANCZOS && desc->lipschitz != DQ_LIP_BOUND)) {
     set_error("dq_solve_noalloc: needs one FP64 or FP32 instance (batch 1) in device memory and device outputs");
     return DQ_ERR_INVALID;
   }

@@ -202,6 +202,7 @@ static void fill_entry(ServeState* S, int e, Ticket& t) {
   I.lmax_Q = c.fresh ? P->lmax_given : P->lmax_Q;
   I.lmin_Q = P->lmin_Q;
   I.normG2 = c.fresh ? P->normG2_given : P->normG2;
+  I.lip_bound = P->lip_bound;
   I.rho = c.rho;
   I.LL = c.LL;
   I.sigma = c.sigma;

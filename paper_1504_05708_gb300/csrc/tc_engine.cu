@@ -156,3 +156,52 @@ extern "C" dq_status dq_test_tc_gemm(const float* A, const float* B, float* D, i
   }
   return DQ_OK;
 }
+
+namespace dq {
+
+// The engines' bounded wait (tc::mbar_wait on the global timer) on an
+// mbarrier that expects one arrival.  complete != 0: thread 0 arrives first,
+// so the wait ends at once; otherwise nothing arrives and the wait gives up
+// after limit_ns.  No copy or MMA is in flight, so giving up is safe.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int complete, int* gave_up) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::mbar_init_fence();
+  }
+  __syncthreads();
+  if (complete && threadIdx.x == 0) tc::mbar_arrive(&bar);
+  const bool ok = tc::mbar_wait(&bar, 0, limit_ns);
+  if (!ok) atomicExch(gave_up, 1);
+}
+
+}  // namespace dq
+
+extern "C" dq_status dq_test_bounded_wait(uint64_t limit_ns, int32_t complete, void* stream) {
+  using namespace dq;
+  if (limit_ns == 0 || limit_ns > 1000000000ull) {
+    set_error("dq_test_bounded_wait: limit_ns must be in (0, 1e9]");
+    return DQ_ERR_INVALID;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  int* flag = nullptr;
+  DQ_CK(cudaMalloc(&flag, sizeof(int)));
+  cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 64, 0, st>>>((unsigned long long)limit_ns, complete, flag);
+    e = cudaGetLastError();
+  }
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(flag);
+  if (e != cudaSuccess) {
+    set_error("dq_test_bounded_wait: %s", cudaGetErrorString(e));
+    return DQ_ERR_CUDA;
+  }
+  if (h) {
+    set_error("dq_test_bounded_wait: the wait gave up after %llu ns", (unsigned long long)limit_ns);
+    return DQ_ERR_TIMEOUT;
+  }
+  return DQ_OK;
+}

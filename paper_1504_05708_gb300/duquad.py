@@ -23,6 +23,7 @@ FP64, FP32, BF16X3 = 0, 1, 2
 INNER_GAP, INNER_FIXED = 0, 1
 CERT_AUTO, CERT_POINT, CERT_STEP = 0, 1, 2
 CONE_INEQ, CONE_EQ = 0, 1
+LIP_LANCZOS, LIP_BOUND = 0, 1
 HOST, DEVICE = 0, 1
 ENGINE_AUTO, ENGINE_CTA, ENGINE_GRID, ENGINE_TC = 0, 1, 2, 3
 OK, NOT_CONVERGED, PENDING = 0, 1, 2
@@ -36,7 +37,8 @@ class ProblemDesc(ctypes.Structure):
                 ("cone", ctypes.c_int32), ("prec", ctypes.c_int32), ("memory", ctypes.c_int32),
                 ("Q", ctypes.c_void_p), ("q", ctypes.c_void_p), ("G", ctypes.c_void_p),
                 ("g", ctypes.c_void_p), ("lb", ctypes.c_void_p), ("ub", ctypes.c_void_p),
-                ("lmax_Q", ctypes.c_double), ("lmin_Q", ctypes.c_double), ("normG2", ctypes.c_double)]
+                ("lmax_Q", ctypes.c_double), ("lmin_Q", ctypes.c_double), ("normG2", ctypes.c_double),
+                ("lipschitz", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -89,7 +91,8 @@ class Stats(ctypes.Structure):
 SYMBOLS = ("dq_context_create", "dq_context_destroy", "dq_problem_create", "dq_problem_set_vectors",
            "dq_problem_constants", "dq_problem_destroy", "dq_solve", "dq_solve_many", "dq_serve_start",
            "dq_submit", "dq_poll", "dq_serve_stop", "dq_context_profile", "dq_context_stats",
-           "dq_autotune", "dq_solve_noalloc", "dq_test_tc_gemm", "dq_theory", "dq_last_error", "dq_version")
+           "dq_autotune", "dq_solve_noalloc", "dq_test_tc_gemm", "dq_test_bounded_wait", "dq_theory",
+           "dq_last_error", "dq_version")
 
 _lib = None
 
@@ -128,6 +131,7 @@ def lib(build_if_needed: bool = True):
     L.dq_serve_stop.argtypes = [vp]
     L.dq_test_tc_gemm.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_int32, vp]
+    L.dq_test_bounded_wait.argtypes = [ctypes.c_uint64, ctypes.c_int32, vp]
     L.dq_autotune.argtypes = [P(vp), ctypes.c_int32, P(SolveOpts), ctypes.c_int32, P(ctypes.c_int32),
                               P(ctypes.c_int32)]
     L.dq_solve_noalloc.argtypes = [ctypes.c_int, P(ProblemDesc), P(SolveOpts), P(Outputs), P(Result), vp]
@@ -249,7 +253,7 @@ class Problem:
     to double); device arrays: torch CUDA tensors of the precision's dtype."""
 
     def __init__(self, ctx: Context, Q, q, G, g, lb, ub, *, prec=FP32, batch=1, cone=CONE_INEQ,
-                 lmax_Q=NAN, lmin_Q=NAN, normG2=NAN):
+                 lmax_Q=NAN, lmin_Q=NAN, normG2=NAN, lipschitz=LIP_LANCZOS):
         self.ctx = ctx
         dev = hasattr(Q, "data_ptr") and getattr(Q, "is_cuda", False)
         n = int(q.shape[-1])
@@ -263,6 +267,7 @@ class Problem:
             keep.append(k)
             setattr(d, f, ptr)
         d.lmax_Q, d.lmin_Q, d.normG2 = lmax_Q, lmin_Q, normG2
+        d.lipschitz = lipschitz
         h = ctypes.c_void_p()
         check(lib().dq_problem_create(ctx.h, ctypes.byref(d), ctypes.byref(h)), (OK,))
         self.h = h

@@ -98,8 +98,10 @@ def test_power_iteration_constants(ctx):
     lmax, lmin, nG2 = P.constants()
     ev = np.linalg.eigvalsh(inst.Q)[-1]
     g2 = np.linalg.norm(inst.G, 2) ** 2
-    assert ev * (1 - 1e-6) <= lmax <= ev * 1.01
-    assert g2 * (1 - 1e-6) <= nG2 <= g2 * 1.01
+    # the estimate is max(theta + 2 r, theta / 0.99) with theta <= lambda_max: an upper bound
+    # (but for a 1e-3 chance) at most about 1 % above
+    assert ev * (1 - 1e-6) <= lmax <= ev * 1.02
+    assert g2 * (1 - 1e-6) <= nG2 <= g2 * 1.02
     assert abs(r.rho - 1.0 / nG2) <= 1e-12 / nG2
 
 

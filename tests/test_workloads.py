@@ -98,3 +98,20 @@ def test_served_stream_is_poisson():
     gaps = np.diff(t)
     assert abs(gaps.mean() - 1 / 2000.0) < 0.05 / 2000.0
     assert abs(kinds.mean() - 0.05) < 0.02
+
+
+def test_hidden_top_eigenvectors_are_orthogonal_to_ones():
+    """The hidden-top generator: Q's and G'G's top eigenvectors are +-(1, -1, 0, ...)/sqrt(2),
+    orthogonal to the all-ones vector, with the stated eigenvalues; Q is symmetric."""
+    inst = W.hidden_top(n=60, p=25, seed=3)
+    v = np.zeros(60)
+    v[:2] = (1.0, -1.0)
+    v /= np.sqrt(2.0)
+    ev, U = np.linalg.eigh(inst.Q)
+    assert np.array_equal(inst.Q, inst.Q.T)
+    assert abs(ev[-1] - 200.0) <= 1e-9 * 200 and ev[-2] <= 100.0 + 1e-9
+    assert abs(abs(U[:, -1] @ v) - 1.0) <= 1e-12 and abs(U[:, -1].sum()) <= 1e-10
+    eg, V = np.linalg.eigh(inst.G.T @ inst.G)
+    assert abs(eg[-1] - 9.0) <= 1e-9 and eg[-2] <= 1.0 + 1e-12
+    assert abs(abs(V[:, -1] @ v) - 1.0) <= 1e-12
+    assert inst.lmin_Q <= ev[0] and ev[0] >= 1.0 - 1e-9

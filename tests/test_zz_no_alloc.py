@@ -44,16 +44,25 @@ def test_noalloc_matches_dq_solve_twice(prec_name, n, p, tol):
     ctx.close()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     desc = _desc(D, t, inst, prec)
-    for call in range(2):  # the scratch keeps the last call's contents; a second call must not see them
+    # call 0 is the set-up call (it loads the library's kernels and the fixed array onto the
+    # device under lazy module loading); calls 1 and 2 must allocate nothing, and the scratch
+    # keeps the last call's contents, which a later call must not see
+    for call in range(3):
         xl = torch.full((n,), float("nan"), dtype=dt, device="cuda")
         xa = torch.full((n,), float("nan"), dtype=dt, device="cuda")
         lm = torch.full((p,), float("nan"), dtype=dt, device="cuda")
         out = D.Outputs()
         out.x_last, out.x_avg, out.lambda_, out.memory = xl.data_ptr(), xa.data_ptr(), lm.data_ptr(), D.DEVICE
         res = D.Result()
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info(0)
         st = D.lib().dq_solve_noalloc(0, ctypes.byref(desc), ctypes.byref(o), ctypes.byref(out), ctypes.byref(res),
                                       stream)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info(0)
         D.check(st)
+        if call > 0:
+            assert free1 == free0, (call, free0, free1)
         assert res.status == r_ref.status == 0
         assert (res.outer_iters, res.inner_iters) == (r_ref.outer_iters, r_ref.inner_iters)
         assert rel(xl.cpu().double().numpy(), xl_ref) <= tol

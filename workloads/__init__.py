@@ -260,3 +260,35 @@ def equality_dense(n=300, p=100, seed=0, lam_lo=1.0, lam_hi=100.0, n_zero=0, box
     inst = Instance(Q, q, G, g, lb, ub, float(lam.min()), float(lam.max()), "ADFGM",
                     {"kind": "equality_dense", "seed": seed, "cone": 1})
     return inst
+
+
+def hidden_top(n=200, p=80, seed=0, lam_lo=1.0, lam_hi=100.0, lam_top=200.0, s_top=3.0):
+    """Dense QP whose Q and G' G have their top eigenvectors orthogonal to the all-ones vector.
+
+    v = (1, -1, 0, ..., 0) / sqrt(2).  Q = P A P + lam_top v v' with P = I - v v' and
+    A = U diag(Lambda) U', Lambda ~ U[lam_lo, lam_hi] (so Q v = lam_top v and the rest of the
+    spectrum lies in [0, lam_hi]); G = W diag(s) V' with V orthogonal, V e_1 = v, s_1 = s_top and
+    the other singular values ~ U[0.1, 1] (so ||G||^2 = s_top^2 along v).  q ~ N(0,1);
+    g = -|N(0,1)| - 0.1; box [-1, 1].  On v-perp, Q acts as A compressed to that subspace, whose
+    eigenvalues lie in [lam_lo, lam_hi] (Cauchy interlacing); lmin_Q is LAPACK's smallest
+    eigenvalue less a 1e-9 relative margin, lmax_Q LAPACK's largest (lam_top)."""
+    rng = np.random.default_rng(seed)
+    v = np.zeros(n)
+    v[0], v[1] = 1.0, -1.0
+    v /= np.sqrt(2.0)
+    U = haar(rng, n)
+    A = (U * rng.uniform(lam_lo, lam_hi, n)[None, :]) @ U.T
+    Pm = np.eye(n) - np.outer(v, v)
+    Q = Pm @ A @ Pm + lam_top * np.outer(v, v)
+    Q = 0.5 * (Q + Q.T)
+    Vb, R = np.linalg.qr(np.column_stack([v, rng.standard_normal((n, n - 1))]))
+    Vb = Vb * np.sign(np.diag(R))[None, :]      # first column is +v
+    Wm = haar(rng, p) if p else np.zeros((0, 0))
+    k = min(n, p)
+    s = np.concatenate([[s_top], rng.uniform(0.1, 1.0, max(k - 1, 0))])[:k]
+    G = (Wm[:, :k] * s[None, :]) @ Vb[:, :k].T if p else np.zeros((0, n))
+    q = rng.standard_normal(n)
+    g = -np.abs(rng.standard_normal(p)) - 0.1
+    ev = np.linalg.eigvalsh(Q)
+    return Instance(Q, q, G, g, -np.ones(n), np.ones(n), float(ev[0]) * (1 - 1e-9), float(ev[-1]), "ADFGM",
+                    {"kind": "hidden_top", "seed": seed})
