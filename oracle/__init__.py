@@ -64,7 +64,8 @@ class _Opts(ctypes.Structure):
                 ("max_inner", ctypes.c_int), ("outer_fixed", ctypes.c_int),
                 ("eps_out", ctypes.c_double), ("outer_check_every", ctypes.c_int),
                 ("max_outer", ctypes.c_int), ("want_last", ctypes.c_int),
-                ("want_avg", ctypes.c_int), ("inner_cert_step", ctypes.c_int)]
+                ("want_avg", ctypes.c_int), ("inner_cert_step", ctypes.c_int),
+                ("stop_fstar", ctypes.c_int), ("f_star", ctypes.c_double)]
 
 
 class _Res(ctypes.Structure):
@@ -279,7 +280,7 @@ class Result:
 def dfom(qp: QP, alg: int, c: Constants, *, inner_fixed=0, eps_in=1e-6, inner_check_every=1,
          max_inner=100000, outer_fixed=0, eps_out=1e-3, outer_check_every=1, max_outer=10000,
          want_last=True, want_avg=True, lambda0=None, x0=None, kd_literal=False,
-         inner_variant=INNER_AUTO, trace_cap=0, inner_cert_step=False) -> Result:
+         inner_variant=INNER_AUTO, trace_cap=0, inner_cert_step=False, f_star=None) -> Result:
     """Algorithm DFOM(d_rho, K_d) (Sec. 3) with both primal outputs (Sec. 4)."""
     o = _Opts()
     o.alg, o.rho, o.LL, o.sigma, o.Ld = alg, c.rho, c.LL, c.sigma, c.Ld
@@ -288,6 +289,8 @@ def dfom(qp: QP, alg: int, c: Constants, *, inner_fixed=0, eps_in=1e-6, inner_ch
     o.outer_fixed, o.eps_out, o.outer_check_every, o.max_outer = outer_fixed, eps_out, outer_check_every, max_outer
     o.want_last, o.want_avg = int(want_last), int(want_avg)
     o.inner_cert_step = int(inner_cert_step)
+    if f_star is not None:  # the paper's stop on |F(u) - F*| (Sec. 6) for a known F*
+        o.stop_fstar, o.f_star = 1, float(f_star)
     n, p = qp.n, qp.p
     xl, xa, lam = np.zeros(n), np.zeros(n), np.zeros(max(p, 1))
     l0 = _f64(lambda0) if (lambda0 is not None and p) else None

@@ -690,3 +690,35 @@ def test_last_iterate_theorem_at_k_out(alg):
         if checked == 3:
             break
     assert checked == 3
+
+
+@pytest.mark.parametrize("alg", ALGS)
+@pytest.mark.parametrize("want", ["last", "avg"])
+def test_fstar_stop_is_the_first_outer_meeting_the_papers_criterion(alg, want):
+    """Sec. 6 stops on |F(u) - F*| <= eps and dist_K(Gu + g) <= eps with F* known: with F* from
+    brute-force KKT the run stops at the first outer iteration whose output meets both (the run
+    one iteration shorter does not), and the returned output meets them when re-scored."""
+    eps = 1e-2
+    done = 0
+    for seed in range(1, 30):
+        inst, qp = _small(seed, n=6, p=4, g_scale=0.02, box=0.3)
+        xs, lam_s, fs = solve_kkt(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+        c = O.constants(qp, alg, lmin_Q=inst.lmin_Q)
+        kw = dict(eps_out=eps, eps_in=O.default_eps_in(alg, eps, c.Ld), max_outer=100000,
+                  want_last=want == "last", want_avg=want == "avg")
+        r = O.dfom(qp, alg, c, f_star=fs, **kw)
+        assert r.status == 0
+        x = r.x_last if want == "last" else r.x_avg
+        assert abs(O.F(qp, x) - fs) <= eps and O.infeas(qp, x) <= eps
+        if r.outer_iters < 2:
+            continue
+        prev = O.dfom(qp, alg, c, outer_fixed=r.outer_iters - 1, **kw)
+        xp = prev.x_last if want == "last" else prev.x_avg
+        assert abs(O.F(qp, xp) - fs) > eps or O.infeas(qp, xp) > eps
+        # the certificate criterion is the stricter one (F - d_lb >= F - F*): never earlier
+        rc = O.dfom(qp, alg, c, **kw)
+        assert rc.outer_iters >= r.outer_iters
+        done += 1
+        if done == 2:
+            break
+    assert done == 2
