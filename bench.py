@@ -5,7 +5,7 @@ Default workload: the single large dense QP (n=20000, p=10000, FP32 iterates,
 FP64 constants and residuals, augmented ADFGM, last iterate and average,
 eps=1e-3).  One step is one pass of the whole hot path on one synthetic
 instance: problem handle over device-resident Q, G (transposed copy built),
-FP64 power iteration for lambda_max(Q) and ||G||^2, the full DFOM solve with
+the Lanczos estimates of lambda_max(Q) and ||G||^2, the full DFOM solve with
 its inner FGM loop, stopping certificates and FP64 residuals.
 
   value    solves/s with inputs already in HBM (CUDA events on the library's stream)
@@ -17,7 +17,8 @@ its inner FGM loop, stopping certificates and FP64 residuals.
   cpu_baseline the FP64 oracle on the host cores on a bounded sample
 
 Other workloads: --workload small (n=50 FP64 DFGM), uneven (10000 mixed QPs,
-one persistent launch), mpc (16384 shared-matrix QPs), served (Poisson stream).
+one persistent launch), mpc (16384 shared-matrix QPs), served (Poisson stream),
+sweep (the paper's eps_in sensitivity and outer-iteration-count studies).
 Multi-GPU: replicas only (independent instances per rank, no collectives).
 """
 from __future__ import annotations
@@ -471,6 +472,122 @@ def run_small(args):
     ctx.close()
 
 
+SWEEP_EPS = 1e-2
+SWEEP_EPS_IN = (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6)
+SWEEP_K = (1, 2, 5, 10, 20, 50, 100, 200, 500)
+SWEEP_N = (10, 50, 100, 200, 300, 400, 500)
+
+
+def run_sweep(args):
+    """The paper's two parameter studies, run as persistent launches on the GPU (FP64, thread-block
+    engine), with F* of every QP from a long FP64 oracle run on the host cores.
+
+    (A) Inner accuracy (Sec. 4, Fig. dfgm_sensitivity): one strongly convex QP (n = 100, p = 50,
+        eps = 1e-2); DGM and DFGM with the inner loop stopped at eps_in in SWEEP_EPS_IN, each run
+        for k outer iterations, k in SWEEP_K; primal suboptimality |F - F*| and dist_K of the
+        average and the last iterate at every (algorithm, eps_in, k).
+    (B) Outer iteration counts (Sec. 6, Fig. comparison_dfo): `count` random QPs (default 25)
+        per n in SWEEP_N (p = n/2, Q > 0, K = R^p_-), eps = 1e-2, stopped as in the paper on
+        |F(u) - F*| <= eps and dist_K(Gu + g) <= eps (stop_fstar), for DGM and DFGM with the
+        last iterate and the average as output: outer iterations per (n, algorithm, output).
+    The table goes to --out (JSON); the printed line's value is study (B)'s solves/s."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import workloads as W
+    from paper_1504_05708_gb300 import duquad as D
+    per_n = args.count or 25
+    stream = torch.cuda.current_stream()
+    ctx = D.Context(0, stream)
+
+    def fstar(inst):  # F(x) of a long FP64 ADFGM run: |F(x) - F*| <= 1e-5, 1e-3 of the studies' eps
+        qp = O.QP(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+        c = O.constants(qp, O.ADFGM, lmin_Q=inst.lmin_Q)
+        r = O.dfom(qp, O.ADFGM, c, eps_out=1e-5, eps_in=1e-9, outer_check_every=5, max_outer=50000,
+                   max_inner=50000)
+        return O.F(qp, r.x_last if r.converged_last else r.x_avg), r.d_lb
+
+    # (A) one QP, algorithms x eps_in x outer counts
+    a_inst = W.single_dense(n=100, p=50, seed=11, g_scale=0.02)
+    insts_b = [(n, W.single_dense(n=n, p=n // 2, seed=5000 + 97 * n + i, g_scale=0.02)) for n in SWEEP_N
+               for i in range(per_n)]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        fs = list(ex.map(fstar, [a_inst] + [i for _, i in insts_b]))
+    oracle_s = time.perf_counter() - t0
+    fa = fs[0][0]
+    a_probs, a_ops, a_keys = [], [], []
+    for alg in ("DGM", "DFGM"):
+        for ein in SWEEP_EPS_IN:
+            for k in SWEEP_K:
+                a_probs.append(D.Problem(ctx, a_inst.Q, a_inst.q, a_inst.G, a_inst.g, a_inst.lb, a_inst.ub,
+                                         prec=D.FP64, lmin_Q=a_inst.lmin_Q))
+                a_ops.append(D.opts(alg, eps_out=SWEEP_EPS, eps_in=ein, fixed_outer=k, max_inner=100000,
+                                    engine=D.ENGINE_CTA))
+                a_keys.append((alg, ein, k))
+    (a_outs, a_res) = D.solve_many(a_probs, a_ops)
+    qa = O.QP(a_inst.Q, a_inst.q, a_inst.G, a_inst.g, a_inst.lb, a_inst.ub)
+    table_a = []
+    for (alg, ein, k), (xl, xa, _), r in zip(a_keys, a_outs, a_res):
+        table_a.append({"alg": alg, "eps_in": ein, "k": k, "inner_iters": int(r.inner_iters),
+                        "subopt_avg": abs(O.F(qa, xa[0]) - fa), "infeas_avg": O.infeas(qa, xa[0]),
+                        "subopt_last": abs(O.F(qa, xl[0]) - fa), "infeas_last": O.infeas(qa, xl[0])})
+    for P in a_probs:
+        P.close()
+    # (B) outer iteration counts at |F - F*| <= eps, dist_K <= eps
+    b_probs, b_ops, b_keys = [], [], []
+    for (n, inst), (f_star, _) in zip(insts_b, fs[1:]):
+        for alg in ("DGM", "DFGM"):
+            for out in (D.OUT_LAST, D.OUT_AVERAGE):
+                b_probs.append(D.Problem(ctx, inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub, prec=D.FP64,
+                                         lmin_Q=inst.lmin_Q))
+                b_ops.append(D.opts(alg, eps_out=SWEEP_EPS, output=out, max_outer=200000, f_star=f_star,
+                                    engine=D.ENGINE_CTA))
+                b_keys.append((n, alg, "last" if out == D.OUT_LAST else "average"))
+    ms, clk, st, res = _timed(ctx, stream, lambda: D.solve_many(b_probs, b_ops), args.steps, args.warmup)
+    b_outs, b_res = res[-1]
+    rows = {}
+    for (n, alg, out), r in zip(b_keys, b_res):
+        rows.setdefault((n, alg, out), []).append(r)
+    table_b = []
+    for (n, alg, out), rs in sorted(rows.items()):
+        it = np.array([r.outer_iters for r in rs], float)
+        table_b.append({"n": n, "p": n // 2, "alg": alg, "output": out, "qps": len(rs),
+                        "converged": sum(1 for r in rs if r.status == 0),
+                        "outer_mean": float(it.mean()), "outer_min": int(it.min()), "outer_max": int(it.max()),
+                        "inner_mean": float(np.mean([r.inner_iters for r in rs]))})
+    # a re-scored check of (B)'s outputs: |F - F*| and dist_K in FP64 by the oracle
+    worst = 0.0
+    for (n, inst), (f_star, _), i in zip(insts_b, fs[1:], range(0, len(b_keys), 4)):
+        qp = O.QP(inst.Q, inst.q, inst.G, inst.g, inst.lb, inst.ub)
+        for j in range(4):
+            xl, xa, _ = b_outs[i + j]
+            x = xl[0] if b_keys[i + j][2] == "last" else xa[0]
+            if b_res[i + j].status == 0:
+                worst = max(worst, abs(O.F(qp, x) - f_star), O.infeas(qp, x))
+    count = len(b_probs)
+    table = {"eps": SWEEP_EPS, "study_A": {"n": 100, "p": 50, "seed": 11, "f_star": fa, "rows": table_a},
+             "study_B": {"per_n": per_n, "rows": table_b, "worst_rescored": worst},
+             "oracle_fstar_seconds": oracle_s}
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    with open(args.out, "w") as f:
+        json.dump(table, f, indent=1)
+    line = _base_line(args, count * args.steps / (ms / 1e3), ms, f"sweep_outer_counts_{per_n}x{len(SWEEP_N)}_fp64",
+                      "f64", {"n": list(SWEEP_N), "p": "n/2", "eps": SWEEP_EPS, "algs": "DGM/DFGM x last/average",
+                              "stop": "|F - F*| <= eps and dist_K <= eps (F* from the FP64 oracle)",
+                              "l2": "all instances fit L2 (latency-bound sweep)"}, clk, st, {
+                          "sweep": {"table": args.out, "worst_rescored": worst,
+                                    "converged": sum(1 for r in b_res if r.status == 0), "solves": count},
+                          "roofline": None, "e2e": None, "cpu_baseline": None})
+    print(json.dumps(line), flush=True)
+    for P in b_probs:
+        P.close()
+    ctx.close()
+
+
 UNEVEN_MAX_OUTER = 50000
 
 
@@ -749,7 +866,9 @@ def run_served(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="large", choices=["large", "eq", "small", "uneven", "mpc", "served"])
+    ap.add_argument("--workload", default="large", choices=["large", "eq", "small", "uneven", "mpc", "served",
+                                                             "sweep"])
+    ap.add_argument("--out", default="gpurun_out/sweep.json", help="sweep workload: where the table goes")
     ap.add_argument("--count", type=int, default=None)
     ap.add_argument("--rate", type=float, default=20000.0)
     ap.add_argument("--duration", type=float, default=0.5)
@@ -786,6 +905,8 @@ def main():
         run_mpc(args)
     elif args.workload == "served":
         run_served(args)
+    elif args.workload == "sweep":
+        run_sweep(args)
     else:
         run_gpu(args)
 

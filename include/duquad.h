@@ -156,6 +156,11 @@ typedef struct {
                               solve instead of reusing the handle's (given
                               values in dq_problem_desc are always kept)       */
   int32_t inner_cert;      /* dq_inner_cert (default DQ_CERT_AUTO)             */
+  int32_t stop_fstar;      /* 1: outer stop on |F(u) - f_star| <= eps_out and
+                              dist_K(Gu+g) <= eps_out instead of the certificate
+                              (the paper's experiments, Sec. 6, for a known F*;
+                              thread-block and grid engines)                   */
+  double f_star;           /* F* for stop_fstar                                */
 } dq_solve_opts;
 
 /* Result of one solve (one instance). */
@@ -192,8 +197,10 @@ dq_status dq_context_destroy(dq_context *ctx);
  * Q and G are borrowed (the caller keeps them alive and unchanged until
  * dq_problem_destroy); vectors are copied.  The library also keeps a
  * transposed copy of G and FP64 constants.  Validation: n >= 1, p >= 0,
- * batch >= 1, lb <= ub (host data), finite values (host data);
- * otherwise DQ_ERR_INVALID.  Errors: DQ_ERR_NOMEM, DQ_ERR_CUDA. */
+ * batch >= 1, and on the device for host and device data alike: finite
+ * values, lb <= ub, and Q symmetric (|Q_ij - Q_ji| <= tol sqrt(|Q_ii Q_jj|),
+ * tol = 1e-10 for FP64, 1e-6 for FP32 and DQ_BF16X3); otherwise DQ_ERR_INVALID
+ * with a message.  Errors: DQ_ERR_NOMEM, DQ_ERR_CUDA. */
 dq_status dq_problem_create(dq_context *ctx, const dq_problem_desc *desc, dq_problem **out);
 
 /* Replace q and/or g (NULL keeps the current one) of all `batch` instances;
@@ -342,6 +349,37 @@ typedef struct {
 } dq_theory_out;
 
 dq_status dq_theory(const dq_theory_in *in, dq_theory_out *out);
+
+/* Theory-mode solve: the method run with the counts of the analysis (Sec. 5,
+ * eq. choose_ein) for one instance (batch 1), with an estimate of R_d where
+ * the caller has none (the paper leaves the R_d search open).
+ *   R_d: Rd > 0 is used as given.  Rd NaN: a certified solve of the same
+ *     instance (algorithm alg, eps_out = eps, default eps_in and rho, from
+ *     lambda^0 = 0) gives multipliers lambda, and R_d = safety *
+ *     max(||lambda||_2, eps) (safety NaN: 2).  A certified lambda can lie short
+ *     of the optimal multipliers, which the safety factor covers.
+ *   D_U = ||ub - lb||_2 of the problem; lmax_Q and normG2 as
+ *     dq_problem_constants gives them; lmin_Q as given at creation (NaN: 0,
+ *     which only ADGM/ADFGM accept).
+ *   rho: NaN takes rho* = 8 R_d^2 / eps for ADGM/ADFGM (0 for DGM/DFGM).
+ * Then a solve with inner_stop = DQ_INNER_FIXED, fixed_outer = k_out,
+ * fixed_inner = k_in, eps_in, rho, L_L, sigma_L and L_d from dq_theory, from
+ * lambda^0 = 0 (no warm start), on `engine` (DQ_ENGINE_AUTO picks as dq_solve),
+ * outputs as in dq_solve.  max_total (0: 1e8) bounds k_out * k_in: larger
+ * counts return DQ_ERR_INVALID before any fixed-count work.  counts and Rd_used
+ * (either may be NULL) receive dq_theory's output and the R_d taken. */
+typedef struct {
+  int32_t alg;          /* dq_algorithm                                      */
+  double eps;           /* target accuracy (> 0)                             */
+  double Rd;            /* > 0, or NaN: estimate                             */
+  double safety;        /* factor on the estimate (NaN: 2)                   */
+  double rho;           /* NaN: rho* (ADGM/ADFGM) or 0                       */
+  int64_t max_total;    /* cap on k_out * k_in (0: 1e8)                      */
+  int32_t engine;       /* dq_engine                                         */
+} dq_theory_solve_opts;
+
+dq_status dq_solve_theory(dq_problem *P, const dq_theory_solve_opts *opts, const dq_outputs *out,
+                          dq_result *result, dq_theory_out *counts, double *Rd_used);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *dq_last_error(void);

@@ -333,6 +333,12 @@ dq_status resolve_opts(const dq_problem* P, const dq_solve_opts* o, SolveCfg* c)
     return DQ_ERR_INVALID;
   }
   c->inner_cert = o->inner_cert;
+  c->stop_fstar = o->stop_fstar != 0;
+  c->f_star = o->f_star;
+  if (c->stop_fstar && !std::isfinite(c->f_star)) {
+    set_error("stop_fstar needs a finite f_star");
+    return DQ_ERR_INVALID;
+  }
   (void)P;
   return DQ_OK;
 }
@@ -748,5 +754,104 @@ dq_status dq_solve_many(dq_problem* const* probs, int32_t count, const dq_solve_
   }
   return cta_solve_problems(probs, count, cfgs.data(), outs, results, smem_cap, threads, true);
 }
+
+static dq_solve_opts default_opts(int alg) {
+  dq_solve_opts o;
+  memset(&o, 0, sizeof(o));
+  o.alg = alg;
+  o.output = DQ_OUT_BOTH;
+  o.eps_out = 1e-3;
+  o.eps_in = NAN;
+  o.rho = NAN;
+  o.Ld = o.LL = o.sigma = NAN;
+  return o;
+}
+
+dq_status dq_solve_theory(dq_problem* P, const dq_theory_solve_opts* t, const dq_outputs* out, dq_result* result,
+                          dq_theory_out* counts, double* Rd_used) {
+  if (!P || !t || !result) {
+    set_error("NULL argument");
+    return DQ_ERR_INVALID;
+  }
+  if (P->batch != 1 || P->prec == DQ_BF16X3) {
+    set_error("dq_solve_theory: one FP64 or FP32 instance (batch 1)");
+    return DQ_ERR_INVALID;
+  }
+  if (!(std::isfinite(t->eps) && t->eps > 0.0) || t->alg < DQ_DGM || t->alg > DQ_ADFGM ||
+      !(std::isnan(t->Rd) || (std::isfinite(t->Rd) && t->Rd > 0.0)) ||
+      !(std::isnan(t->safety) || (std::isfinite(t->safety) && t->safety > 0.0)) || t->max_total < 0) {
+    set_error("dq_solve_theory: invalid algorithm, eps, R_d, safety or max_total");
+    return DQ_ERR_INVALID;
+  }
+  DQ_CK(cudaSetDevice(P->ctx->device));
+  const size_t n = P->n, p = P->p;
+  double Rd = t->Rd;
+  dq_status s;
+  if (std::isnan(Rd)) {  // R_d from the multipliers of a certified solve
+    dq_solve_opts o = default_opts(t->alg);
+    o.eps_out = t->eps;
+    o.engine = t->engine;
+    std::vector<double> lam(std::max<size_t>(p, 1));
+    dq_outputs lo;
+    memset(&lo, 0, sizeof(lo));
+    lo.lambda = lam.data();
+    lo.memory = DQ_HOST;
+    dq_result r;
+    s = dq_solve(P, &o, &lo, &r);
+    if (s < 0) return s;
+    double nl = 0.0;
+    for (size_t j = 0; j < p; ++j) nl += lam[j] * lam[j];
+    Rd = (std::isnan(t->safety) ? 2.0 : t->safety) * std::max(std::sqrt(nl), t->eps);
+  }
+  // D_U = ||ub - lb||_2 from the handle's device copies
+  std::vector<double> lb(n), ub(n);
+  if (P->esz == 8) {
+    DQ_CK(cudaMemcpyAsync(lb.data(), P->lb, n * 8, cudaMemcpyDeviceToHost, P->ctx->stream));
+    DQ_CK(cudaMemcpyAsync(ub.data(), P->ub, n * 8, cudaMemcpyDeviceToHost, P->ctx->stream));
+    DQ_CK(cudaStreamSynchronize(P->ctx->stream));
+  } else {
+    std::vector<float> f(2 * n);
+    DQ_CK(cudaMemcpyAsync(f.data(), P->lb, n * 4, cudaMemcpyDeviceToHost, P->ctx->stream));
+    DQ_CK(cudaMemcpyAsync(f.data() + n, P->ub, n * 4, cudaMemcpyDeviceToHost, P->ctx->stream));
+    DQ_CK(cudaStreamSynchronize(P->ctx->stream));
+    for (size_t i = 0; i < n; ++i) {
+      lb[i] = f[i];
+      ub[i] = f[n + i];
+    }
+  }
+  double D2 = 0.0;
+  for (size_t i = 0; i < n; ++i) D2 += (ub[i] - lb[i]) * (ub[i] - lb[i]);
+  dq_theory_in ti;
+  ti.alg = t->alg;
+  ti.eps = t->eps;
+  ti.Rd = Rd;
+  ti.D_U = std::sqrt(D2);
+  ti.rho = t->rho;
+  if ((s = dq_problem_constants(P, &ti.lmax_Q, &ti.lmin_Q, &ti.normG2)) != DQ_OK) return s;
+  if (std::isnan(ti.lmin_Q)) ti.lmin_Q = 0.0;
+  if (!(ti.D_U > 0.0)) ti.D_U = 1e-300;  // a box of one point: any count is enough
+  dq_theory_out to;
+  if ((s = dq_theory(&ti, &to)) != DQ_OK) return s;
+  if (counts) *counts = to;
+  if (Rd_used) *Rd_used = Rd;
+  const int64_t cap = t->max_total > 0 ? t->max_total : 100000000LL;
+  if (to.k_total > cap || to.k_out > INT32_MAX || to.k_in > INT32_MAX) {
+    set_error("dq_solve_theory: k_out * k_in = %lld exceeds the cap %lld", (long long)to.k_total, (long long)cap);
+    return DQ_ERR_INVALID;
+  }
+  dq_solve_opts o = default_opts(t->alg);
+  o.inner_stop = DQ_INNER_FIXED;
+  o.fixed_outer = (int32_t)to.k_out;
+  o.fixed_inner = (int32_t)to.k_in;
+  o.eps_out = t->eps;
+  o.eps_in = to.eps_in;
+  o.rho = to.rho;
+  o.LL = to.LL;
+  o.sigma = to.sigma;
+  o.Ld = to.Ld;
+  o.engine = t->engine;
+  return dq_solve(P, &o, out, result);
+}
+
 
 }  // extern "C"

@@ -34,6 +34,8 @@ struct CtaInst {
   const T *q, *g, *lb, *ub;       // device vectors
   double lmax_Q, lmin_Q, normG2;  // NaN lmax_Q / normG2: Lanczos estimate (or bound) on chip
   int lip_bound;                  // 1: guaranteed bounds instead of the Lanczos estimate
+  int stop_fstar;                 // 1: outer stop on |F - f_star| instead of F - d_lb
+  double f_star;
   double rho;                     // NaN: 0 for DGM/DFGM, 1/||G||^2 for ADGM/ADFGM
   double LL, sigma, Ld;           // NaN: derived (Sec. 3 Step 1, eq. Ld)
   int inner_fixed, inner_check_every, max_inner;
@@ -816,8 +818,11 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
         done = true;
       }
       if (I.outer_fixed <= 0 && !done) {
-        conv_last = I.want_last && i_last <= I.eps_out && f_last - d_lb <= I.eps_out;
-        conv_avg = I.want_avg && i_avg <= I.eps_out && f_avg - d_lb <= I.eps_out;
+        // the certificate F - d_lb, or |F - F*| for a known F* (the paper's experiments)
+        const double gl = I.stop_fstar ? fabs(f_last - I.f_star) : f_last - d_lb;
+        const double ga = I.stop_fstar ? fabs(f_avg - I.f_star) : f_avg - d_lb;
+        conv_last = I.want_last && i_last <= I.eps_out && gl <= I.eps_out;
+        conv_avg = I.want_avg && i_avg <= I.eps_out && ga <= I.eps_out;
         done = conv_last || conv_avg;
       }
     }

@@ -138,6 +138,8 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
       I.lmin_Q = lmin;
       I.normG2 = c.fresh ? P->normG2_given : P->normG2;
       I.lip_bound = P->lip_bound;
+      I.stop_fstar = c.stop_fstar;
+      I.f_star = c.f_star;
       I.rho = c.rho;
       I.LL = c.LL;
       I.sigma = c.sigma;

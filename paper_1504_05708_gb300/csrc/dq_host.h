@@ -51,6 +51,8 @@ struct SolveCfg {
   int warm_start, kd_literal, fresh;
   int inner_cert;  // dq_inner_cert
   double Ld, LL, sigma;
+  int stop_fstar;  // outer stop on |F - f_star| (Sec. 6 experiments) instead of the certificate
+  double f_star;
 };
 
 }  // namespace dq

@@ -1347,8 +1347,10 @@ struct GridRun {
           done = true;
         }
         if (cfg->fixed_outer <= 0 && !done) {
-          conv_last = want_last && i_last <= cfg->eps_out && f_last - d_lb <= cfg->eps_out;
-          conv_avg = want_avg && i_avg <= cfg->eps_out && f_avg - d_lb <= cfg->eps_out;
+          const double gl = cfg->stop_fstar ? fabs(f_last - cfg->f_star) : f_last - d_lb;
+          const double ga = cfg->stop_fstar ? fabs(f_avg - cfg->f_star) : f_avg - d_lb;
+          conv_last = want_last && i_last <= cfg->eps_out && gl <= cfg->eps_out;
+          conv_avg = want_avg && i_avg <= cfg->eps_out && ga <= cfg->eps_out;
           done = conv_last || conv_avg;
         }
       }

@@ -123,6 +123,8 @@ static dq_status run_noalloc(int device, const dq_problem_desc* d, const SolveCf
   I.lmin_Q = d->lmin_Q;
   I.normG2 = d->normG2;
   I.lip_bound = d->lipschitz == DQ_LIP_BOUND;
+  I.stop_fstar = c.stop_fstar;
+  I.f_star = c.f_star;
   I.rho = c.rho;
   I.LL = c.LL;
   I.sigma = c.sigma;

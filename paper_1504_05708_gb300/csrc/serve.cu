@@ -203,6 +203,8 @@ static void fill_entry(ServeState* S, int e, Ticket& t) {
   I.lmin_Q = P->lmin_Q;
   I.normG2 = c.fresh ? P->normG2_given : P->normG2;
   I.lip_bound = P->lip_bound;
+  I.stop_fstar = c.stop_fstar;
+  I.f_star = c.f_star;
   I.rho = c.rho;
   I.LL = c.LL;
   I.sigma = c.sigma;

@@ -930,6 +930,10 @@ dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_r
     set_error("the tensor-core engine needs rho = 0");
     return DQ_ERR_INVALID;
   }
+  if (c.stop_fstar) {
+    set_error("the tensor-core engine stops on the certificate only (no stop_fstar)");
+    return DQ_ERR_INVALID;
+  }
   const int n = P->n, p = P->p, B = P->batch;
   if ((n + 15) / 16 * 16 > 128) {
     set_error("the tensor-core engine holds n <= 128 variables per instance in tensor memory (n = %d)", n);

@@ -49,7 +49,8 @@ class SolveOpts(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("inner_check_every", ctypes.c_int32),
                 ("warm_start", ctypes.c_int32), ("kd_literal", ctypes.c_int32),
                 ("Ld", ctypes.c_double), ("LL", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("fresh_constants", ctypes.c_int32), ("inner_cert", ctypes.c_int32)]
+                ("fresh_constants", ctypes.c_int32), ("inner_cert", ctypes.c_int32),
+                ("stop_fstar", ctypes.c_int32), ("f_star", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -82,6 +83,12 @@ class TheoryOut(ctypes.Structure):
                 ("k_in", ctypes.c_int64), ("k_total", ctypes.c_int64)]
 
 
+class TheorySolveOpts(ctypes.Structure):
+    _fields_ = [("alg", ctypes.c_int32), ("eps", ctypes.c_double), ("Rd", ctypes.c_double),
+                ("safety", ctypes.c_double), ("rho", ctypes.c_double), ("max_total", ctypes.c_int64),
+                ("engine", ctypes.c_int32)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("gemv_launches", ctypes.c_int64), ("gemv_ms", ctypes.c_double),
                 ("gemv_bytes", ctypes.c_double), ("reduce_launches", ctypes.c_int64),
@@ -92,7 +99,7 @@ SYMBOLS = ("dq_context_create", "dq_context_destroy", "dq_problem_create", "dq_p
            "dq_problem_constants", "dq_problem_destroy", "dq_solve", "dq_solve_many", "dq_serve_start",
            "dq_submit", "dq_poll", "dq_serve_stop", "dq_context_profile", "dq_context_stats",
            "dq_autotune", "dq_solve_noalloc", "dq_test_tc_gemm", "dq_test_bounded_wait", "dq_theory",
-           "dq_last_error", "dq_version")
+           "dq_solve_theory", "dq_last_error", "dq_version")
 
 _lib = None
 
@@ -138,6 +145,8 @@ def lib(build_if_needed: bool = True):
     L.dq_context_profile.argtypes = [vp, ctypes.c_int32]
     L.dq_context_stats.argtypes = [vp, P(Stats), ctypes.c_int32]
     L.dq_theory.argtypes = [P(TheoryIn), P(TheoryOut)]
+    L.dq_solve_theory.argtypes = [vp, P(TheorySolveOpts), P(Outputs), P(Result), P(TheoryOut),
+                                  P(ctypes.c_double)]
     for name in SYMBOLS[:-2]:
         getattr(L, name).restype = st
     L.dq_last_error.restype = ctypes.c_char_p
@@ -175,7 +184,7 @@ def _ptr(a):
 def opts(alg="DFGM", *, output=OUT_BOTH, inner_stop=INNER_GAP, engine=ENGINE_AUTO, eps_out=1e-3,
          eps_in=NAN, rho=NAN, fixed_outer=0, fixed_inner=0, max_outer=0, max_inner=0, check_every=0,
          inner_check_every=0, warm_start=0, kd_literal=0, Ld=NAN, LL=NAN, sigma=NAN,
-         fresh_constants=0, inner_cert=CERT_AUTO) -> SolveOpts:
+         fresh_constants=0, inner_cert=CERT_AUTO, f_star=None) -> SolveOpts:
     o = SolveOpts()
     o.alg = ALGS[alg] if isinstance(alg, str) else int(alg)
     o.output, o.inner_stop, o.engine = output, inner_stop, engine
@@ -184,6 +193,8 @@ def opts(alg="DFGM", *, output=OUT_BOTH, inner_stop=INNER_GAP, engine=ENGINE_AUT
     o.check_every, o.inner_check_every, o.warm_start, o.kd_literal = check_every, inner_check_every, warm_start, kd_literal
     o.Ld, o.LL, o.sigma = Ld, LL, sigma
     o.fresh_constants = fresh_constants
+    if f_star is not None:  # the paper's stop on |F(u) - F*| for a known F*
+        o.stop_fstar, o.f_star = 1, float(f_star)
     o.inner_cert = inner_cert
     if fixed_inner and inner_stop == INNER_GAP:
         o.inner_stop = INNER_FIXED
@@ -312,6 +323,19 @@ class Problem:
         if B == 1:
             return xl[0], xa[0], lm[0], [res[0]]
         return xl, xa, lm, list(res)
+
+    def solve_theory(self, alg, eps, *, Rd=NAN, safety=NAN, rho=NAN, max_total=0, engine=ENGINE_AUTO):
+        """dq_solve_theory: the fixed counts of the analysis (with an R_d estimate when Rd is NaN).
+        Returns (x_last, x_avg, lam, Result, counts dict, R_d used)."""
+        t = TheorySolveOpts(ALGS[alg] if isinstance(alg, str) else int(alg), eps, Rd, safety, rho, max_total,
+                            engine)
+        xl, xa, lm = np.zeros(self.n), np.zeros(self.n), np.zeros(max(self.p, 1))
+        out = Outputs()
+        out.x_last, out.x_avg, out.lambda_, out.memory = xl.ctypes.data, xa.ctypes.data, lm.ctypes.data, HOST
+        r, to, rd = Result(), TheoryOut(), ctypes.c_double()
+        check(lib().dq_solve_theory(self.h, ctypes.byref(t), ctypes.byref(out), ctypes.byref(r), ctypes.byref(to),
+                                    ctypes.byref(rd)))
+        return xl, xa, lm[:self.p], r, {f: getattr(to, f) for f, _ in TheoryOut._fields_}, rd.value
 
     def close(self):
         if getattr(self, "h", None):
