@@ -109,6 +109,11 @@ struct dq_problem {
   double lmax_Q = NAN, lmin_Q = NAN, normG2 = NAN;
   double lmax_given = NAN, normG2_given = NAN;  // as passed in dq_problem_desc
   int lip_bound = 0;                            // dq_problem_desc.lipschitz == DQ_LIP_BOUND
+  // sparse (CSR) problems: Q, G, GT above hold the value arrays; row offsets
+  // and column indices here (int32, device); solved by the grid engine only
+  bool sparse = false;
+  int *q_rp = nullptr, *q_ci = nullptr, *g_rp = nullptr, *g_ci = nullptr, *gt_rp = nullptr, *gt_ci = nullptr;
+  long long nnzQ = 0, nnzG = 0;
   dq::GridWs* gws = nullptr;
   dq::TcWs* tws = nullptr;
   std::mutex mu;

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "dq_host.h"
+#include "csr.cuh"
 #include "grid_v2.cuh"
 
 namespace dq {
@@ -81,32 +82,45 @@ struct RowJob {
   const int* done;             // non-null: return at once when *done != 0
 };
 
+// Element i of the prologue vector of a product.
+template <typename T>
+__device__ __forceinline__ T form_one(const RowJob<T>& J, int i) {
+  const T b = J.beta;
+  if (J.vmode == VM_STEP) {  // x^k = [y - (Q y + add) / L]_U
+    const T x = J.a0[i], xp = J.a1[i], qx = J.a2[i], qxp = J.a3[i];
+    const T y = x + b * (x - xp);
+    const T qy = qx + b * (qx - qxp);
+    const T gr = qy + J.a4[i] + (J.a5 ? J.a5[i] : T(0));
+    const T t = y - gr / J.L;
+    return t < J.a6[i] ? J.a6[i] : (t > J.a7[i] ? J.a7[i] : t);
+  }
+  if (J.vmode == VM_W) {  // w = [mu + rho (G y + g)]_K*
+    const T gx = J.a0[i], gxp = J.a1[i];
+    const T gy = gx + b * (gx - gxp);
+    const T t = J.a2[i] + J.rho * (gy + J.a3[i]);
+    return J.cone == CONE_EQ ? t : (t > T(0) ? t : T(0));
+  }
+  return J.a0[i];
+}
+
 // Prologue: the vector v (length len) in shared memory.
 template <typename T>
 __device__ __forceinline__ void form_vector(const RowJob<T>& J, T* v, int len) {
-  const T b = J.beta;
   const int chunk = (len + gridDim.x - 1) / gridDim.x;
   const int lo = blockIdx.x * chunk, hi = min(len, lo + chunk);
   for (int i = threadIdx.x; i < len; i += blockDim.x) {
-    T val;
-    if (J.vmode == VM_STEP) {  // x^k = [y - (Q y + add) / L]_U
-      const T x = J.a0[i], xp = J.a1[i], qx = J.a2[i], qxp = J.a3[i];
-      const T y = x + b * (x - xp);
-      const T qy = qx + b * (qx - qxp);
-      const T gr = qy + J.a4[i] + (J.a5 ? J.a5[i] : T(0));
-      const T t = y - gr / J.L;
-      val = t < J.a6[i] ? J.a6[i] : (t > J.a7[i] ? J.a7[i] : t);
-    } else if (J.vmode == VM_W) {  // w = [mu + rho (G y + g)]_K*
-      const T gx = J.a0[i], gxp = J.a1[i];
-      const T gy = gx + b * (gx - gxp);
-      const T t = J.a2[i] + J.rho * (gy + J.a3[i]);
-      val = J.cone == CONE_EQ ? t : (t > T(0) ? t : T(0));
-    } else {
-      val = J.a0[i];
-    }
+    const T val = form_one<T>(J, i);
     v[i] = val;
     if (J.vout && i >= lo && i < hi) J.vout[i] = val;
   }
+}
+
+// Sparse products: the whole prologue vector into global memory (`out`; the
+// job's vout when it asks for the vector, else a workspace vector).
+template <typename T>
+__global__ void __launch_bounds__(256) k_csr_form(RowJob<T> J, int len, T* out) {
+  if (J.done && *(volatile const int*)J.done) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < len; i += gridDim.x * blockDim.x) out[i] = form_one<T>(J, i);
 }
 
 // Row-dot GEMV over the rows of M1 then M2 with the prologue vector.  One
@@ -603,6 +617,7 @@ struct GridWs {
   void *c, *tn, *w, *whi, *wlo, *mu, *lam, *lamp, *ul, *uavg, *pv, *pw, *pt;
   double *usum, *dQ, *dG, *gwh, *gwl;
   double* lzrec = nullptr;  // alpha_j, beta_j of the Lanczos runs (2 kLzMaxSteps)
+  void* vsp = nullptr;      // prologue vector of the sparse products (max(n, p) elements)
   int blocks = 0;
   // single-pass (v2) layout: packed upper triangle of Q and partial sums
   void* v2mem = nullptr;
@@ -650,7 +665,8 @@ static dq_status grid_ws(dq_problem* P, GridWs** out) {
   auto a256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t vn = a256(n * W->esz), vp = a256(pn * W->esz), dn = a256(n * 8), dp = a256(pn * 8);
   const size_t total = 12 * vn + 6 * vp + 3 * vn /*c tn ul*/ + 2 * vn /*uavg pv*/ + vn /*pw*/ + vp /*pt*/ +
-                       6 * vp /*w whi wlo mu lam lamp*/ + 4 * dn /*usum dQ gwh gwl*/ + dp /*dG*/;
+                       6 * vp /*w whi wlo mu lam lamp*/ + 4 * dn /*usum dQ gwh gwl*/ + dp /*dG*/ +
+                       (P->sparse ? std::max(vn, vp) : 0) /*vsp*/;
   if (cudaMalloc(&W->mem, total) != cudaSuccess) {
     cudaGetLastError();
     delete W;
@@ -672,6 +688,7 @@ static dq_status grid_ws(dq_problem* P, GridWs** out) {
   W->w = take(vp); W->whi = take(vp); W->wlo = take(vp); W->mu = take(vp); W->lam = take(vp); W->lamp = take(vp);
   W->usum = (double*)take(dn); W->dQ = (double*)take(dn); W->gwh = (double*)take(dn); W->gwl = (double*)take(dn);
   W->dG = (double*)take(dp);
+  if (P->sparse) W->vsp = take(std::max(vn, vp));
   W->blocks = P->ctx->num_sms * 2;
   if (cudaMalloc(&W->ctrl, sizeof(Ctrl)) != cudaSuccess || cudaMallocHost(&W->hctrl, 2 * sizeof(Ctrl)) != cudaSuccess ||
       cudaMalloc(&W->lzrec, sizeof(double) * 2 * kLzMaxSteps) != cudaSuccess ||
@@ -711,8 +728,40 @@ struct GridRun {
   const T* ub() const { return (const T*)P->ub; }
   T* v(void* a) const { return (T*)a; }
 
+  // CSR structure of one of the problem's value arrays (Q, G or G')
+  CsrRef csr_of(const T* M) const {
+    if (M == (const T*)P->Q) return CsrRef{P->q_rp, P->q_ci};
+    if (M == (const T*)P->G) return CsrRef{P->g_rp, P->g_ci};
+    return CsrRef{P->gt_rp, P->gt_ci};
+  }
+  template <bool ACC, int TPR>
+  void csr_launch(const RowJob<T>& J, CsrRef A1, CsrRef A2, const T* v) {
+    k_csr_rows<T, ACC, TPR, RowJob<T>><<<blocks * 8, 256, 0, st>>>(J, A1, A2, v);
+  }
+  template <bool ACC>
+  cudaError_t rows_csr(const RowJob<T>& J) {
+    T* v = J.vout ? J.vout : (T*)W->vsp;
+    k_csr_form<T><<<std::min(blocks * 8, (J.cols + 255) / 256 + 1), 256, 0, st>>>(J, J.cols, v);
+    const CsrRef A1 = csr_of(J.M1), A2 = J.M2 ? csr_of(J.M2) : CsrRef{nullptr, nullptr};
+    // lanes per row from the mean row length of the products' matrices
+    const long long nnz = (long long)((A1.rp == P->q_rp) ? P->nnzQ : (A1.rp == P->g_rp ? P->nnzG : P->nnzG)) +
+                          (J.M2 ? P->nnzG : 0);
+    const double avg = double(nnz) / std::max(1, J.R1 + J.R2);
+    const int tpr = avg > 24 ? 32 : avg > 12 ? 16 : avg > 6 ? 8 : avg > 3 ? 4 : 2;
+    switch (tpr) {
+      case 32: csr_launch<ACC, 32>(J, A1, A2, v); break;
+      case 16: csr_launch<ACC, 16>(J, A1, A2, v); break;
+      case 8: csr_launch<ACC, 8>(J, A1, A2, v); break;
+      case 4: csr_launch<ACC, 4>(J, A1, A2, v); break;
+      default: csr_launch<ACC, 2>(J, A1, A2, v); break;
+    }
+    P->ctx->launches += 2;
+    return cudaGetLastError();
+  }
+
   template <bool ACC>
   cudaError_t rows(RowJob<T> J) {
+    if (P->sparse) return rows_csr<ACC>(J);
     size_t smem = (size_t)J.cols * sizeof(T);
     auto kern = k_rows<T, ACC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -808,6 +857,10 @@ struct GridRun {
   // ||G||_F^2), from FP64 column sums on the device (Q symmetric: column sums
   // are row sums; G' has G's row sums as its column sums).
   dq_status bound(int which, double* out) {
+    if (P->sparse) {  // sparse problems take their bounds at creation (host CSR)
+      set_error("internal: dense bound on a sparse problem");
+      return DQ_ERR_INVALID;
+    }
     auto colmax = [&](const T* M, int rows, int cols, double* mx, double* fro) -> dq_status {
       const int segs = 32;
       void* buf = nullptr;
@@ -904,7 +957,7 @@ struct GridRun {
     v2_npt = std::max(2, ((n4 + V2_CONS - 1) / V2_CONS + 1) / 2 * 2);
     // xs: the four x of each of a Q-CTA's blocks (blocks dealt round-robin), or a G-CTA's row constants
     const size_t xs_len = std::max<size_t>(4 * (size_t)((nb + nQ - 1) / nQ), nG > 0 ? (size_t)(p + nG - 1) / nG : 0) + 4;
-    // the ring (V2_STAGES stages of 16 KB) and xs must fit in shared memory, else
+    // the ring (V2_STAGES stages of 32 KB) and xs must fit in shared memory, else
     // the two-pass form runs (xs grows with p / nG for very wide G)
     v2_smem = (size_t)V2_STAGES * V2_CH4 * 16 + xs_len * 4 + 256;
     if (v2_smem > max_dynamic_smem(v2_kernel(), P->ctx->smem_optin)) use_v2 = false;
@@ -1454,12 +1507,12 @@ static dq_status solve_T(dq_problem* P, GridWs* W, const SolveCfg& c, const dq_o
     // n <= 20480) use the single-pass iteration; DQ_GRID_SINGLE_PASS=0 selects
     // the two-pass form (kept as the reference path of the tests)
     const char* ev = getenv("DQ_GRID_SINGLE_PASS");
-    R.use_v2 = (P->n % 4 == 0) && (P->n / 4 <= V2_CONS * 10) && !(ev && ev[0] == '0');
+    R.use_v2 = !P->sparse && (P->n % 4 == 0) && (P->n / 4 <= V2_CONS * 10) && !(ev && ev[0] == '0');
   }
   // K = {0} with rho > 0: precompute H = Q + rho G'G (DQ_GRID_HESSIAN=0 keeps the
   // augmented two-matrix form, the reference path of the tests)
   const char* eh = getenv("DQ_GRID_HESSIAN");
-  R.hmode = P->cone == CONE_EQ && R.rho > 0.0 && P->p > 0 && !(eh && eh[0] == '0');
+  R.hmode = !P->sparse && P->cone == CONE_EQ && R.rho > 0.0 && P->p > 0 && !(eh && eh[0] == '0');
   return R.solve(out, res);
 }
 

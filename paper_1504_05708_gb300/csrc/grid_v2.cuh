@@ -16,15 +16,18 @@
 //     G' w of the next iteration.
 // A CTA is either a Q-CTA (blocks c, c + nQ, c + 2 nQ, ...: every Q-CTA gets
 // the same mix of long and short blocks) or a G-CTA (a contiguous range of G
-// rows).  Data streams through a ring of 16 KB shared-memory stages filled by
-// bulk copies (full/empty mbarrier pairs): thread 0 fills the ring at the
+// rows).  Data streams through a ring of six 32 KB shared-memory stages filled
+// by bulk copies (full/empty mbarrier pairs): thread 0 fills the ring at the
 // start, and refills a stage as soon as all 16 warps have released it, so up
 // to 192 KB per SM are in flight.  (A separate producer warp would make 17
 // warps per CTA and cut the register budget from 128 to 96 per thread.)  A
-// chunk covers 1024 columns of a Q block (G: 1024 float4 of a row) at a fixed
-// global position, which is two of each thread's register-resident column
+// chunk covers 2048 columns of a Q block (G: 2048 float4 of a row) at a fixed
+// global position, which is four of each thread's register-resident column
 // slots (Q: column t + 512 m; G: float4 column t + 512 m): the iterate x^k
-// and the column partial sums never leave registers.  Each CTA writes one
+// and the column partial sums never leave registers.  Each wait on a stage
+// and each release serve four float4 per thread: with 16 KB chunks (two per
+// thread) the loop control per byte was twice as large and the kernel ran at
+// 0.73 of the measured HBM bandwidth instead of 0.90 at n = 20000.  Each CTA writes one
 // partial vector; k_v2_reduce adds the partial vectors in a fixed order
 // (deterministic) and the row dots, and forms the next iterate x^{k+1} from
 // them, so a pass reads only x^k besides the matrices.  HBM bytes per
@@ -65,10 +68,10 @@ struct V2Args {
 
 static constexpr int V2_CONS = 512;                 // threads (16 warps), all consumers
 static constexpr int V2_THREADS = V2_CONS;
-static constexpr int V2_CH4 = 2 * V2_CONS;          // chunk: 1024 x 16 bytes (16 KB)
-static constexpr int V2_STAGES = 12;                // ring depth (192 KB); a compile-time depth
-                                                    // ran 8 % faster than the same depth passed
-                                                    // at run time
+static constexpr int V2_CW = 4;                     // float4 of a chunk per thread
+static constexpr int V2_CH4 = V2_CW * V2_CONS;      // chunk: 2048 x 16 bytes (32 KB)
+static constexpr int V2_STAGES = 6;                 // ring depth (192 KB), a compile-time constant
+                                                    // (a depth passed at run time cost 8 %)
 static constexpr int V2_RB = 16;                    // Q blocks (64 rows) between flushes of the row dots
 static constexpr unsigned long long V2_WAIT_NS = 2000000000ull;
 
@@ -91,12 +94,14 @@ __device__ __forceinline__ void v2_kahan(float& s, float& c, float v) {
   s = t;
 }
 
-// NPT (even) float4 column slots per thread for G rows (2 per G chunk); a Q
-// block spans at most 2 NPT chunks (4 NPT scalar column slots per thread).
+// NPT float4 column slots per thread for G rows (V2_CW of them per chunk); a
+// Q-CTA thread holds 4 NPT scalar column slots (V2_CW per chunk).
 template <int NPT>
 __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
-  static_assert(NPT % 2 == 0 && NPT / 2 < V2_STAGES, "chunk ring too shallow");
-  constexpr int NQS = 4 * NPT;  // scalar column slots of a Q-CTA thread
+  constexpr int NQS = 4 * NPT;                          // scalar column slots of a Q-CTA thread
+  constexpr int NQC = (NQS + V2_CW - 1) / V2_CW;        // chunk positions of a Q block
+  constexpr int NGC = (NPT + V2_CW - 1) / V2_CW;        // chunk positions of a G row
+  static_assert(NGC < V2_STAGES, "chunk ring too shallow");
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(8) uint64_t full[V2_STAGES], empty[V2_STAGES];
   __shared__ float4 sdot[V2_RB][V2_CONS / 32];
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
     if (!stop && a.cprev) {
       float v = 0.f;
       for (int i = lane; i < a.ncert; i += 32) v += __ldcg(a.cprev + i);
-      v = v2_warp_sum(v);  // butterfly: the same bits in every lane and every CTA
+      v = v2_warp_sum(v);
       const float ct = a.ccoef * v;
       if (ct <= a.eps_in || a.kprev >= a.kmax) {
         stop = 1;
@@ -142,7 +147,6 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
     tc::mbar_init_fence();
   }
   __syncthreads();
-
   // Issue cursor (thread 0 only): chunk pk of this CTA's pr-th unit (Q block
   // or G row), whose data starts at u_src (column / float4 column u_f0).
   // Stages are refilled in the order they are released, so the chunk issued
@@ -226,32 +230,32 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
         const int blk = c + idx * nQ;
         const int f0 = 4 * blk, kf = f0 / V2_CH4;
         const float4 xq = *(const float4*)(xs + 4 * idx);
-        // four row dots, two FP32 accumulators each (even / odd half of every
+        // four row dots, two FP32 accumulators each (even / odd slots of every
         // chunk): a thread adds at most 2 NPT small products per accumulator
         float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;
 #pragma unroll
-        for (int k = 0; k < 2 * NPT; ++k) {
+        for (int k = 0; k < NQC; ++k) {
           if (k >= kf && k <= klq) {  // the same for every thread of the CTA
             ok = tc::mbar_wait(&full[rs], rph, V2_WAIT_NS) && ok;
-            const float4* ch = ring + (size_t)rs * V2_CH4;  // columns k CH4 + t and k CH4 + t + CONS
-            const int m0 = 2 * k, ja = t + V2_CONS * m0, jb = ja + V2_CONS;
-            float4 va = ch[t], vb = ch[t + V2_CONS];
-            if (k == kf || k == klq) {  // left of the block's first column, or past n: zero
-              if (ja < f0 || ja >= n) va = z4;
-              if (jb < f0 || jb >= n) vb = z4;
+            const float4* ch = ring + (size_t)rs * V2_CH4;
+            const bool edge = (k == kf || k == klq);
+#pragma unroll
+            for (int h = 0; h < V2_CW; ++h) {
+              const int m = V2_CW * k + h;
+              if (m < NQS) {
+                const int j = t + V2_CONS * m;
+                float4 v = ch[t + V2_CONS * h];  // column k CH4 + t + CONS h = slot m
+                if (edge && (j < f0 || j >= n)) v = z4;  // left of the block's first column, or past n
+                const float xa = xv[m];
+                if (h & 1) {
+                  e0 = fmaf(v.x, xa, e0); e1 = fmaf(v.y, xa, e1); e2 = fmaf(v.z, xa, e2); e3 = fmaf(v.w, xa, e3);
+                } else {
+                  s0 = fmaf(v.x, xa, s0); s1 = fmaf(v.y, xa, s1); s2 = fmaf(v.z, xa, s2); s3 = fmaf(v.w, xa, s3);
+                }
+                // column update x_{4b+r} Q[4b+r, j]
+                pv[m] = fmaf(xq.x, v.x, fmaf(xq.y, v.y, fmaf(xq.z, v.z, fmaf(xq.w, v.w, pv[m]))));
+              }
             }
-            const float xa = xv[m0], xb = xv[m0 + 1];
-            s0 = fmaf(va.x, xa, s0);
-            e0 = fmaf(vb.x, xb, e0);
-            s1 = fmaf(va.y, xa, s1);
-            e1 = fmaf(vb.y, xb, e1);
-            s2 = fmaf(va.z, xa, s2);
-            e2 = fmaf(vb.z, xb, e2);
-            s3 = fmaf(va.w, xa, s3);
-            e3 = fmaf(vb.w, xb, e3);
-            // column updates x_{4b+r} Q[4b+r, j]
-            pv[m0] = fmaf(xq.x, va.x, fmaf(xq.y, va.y, fmaf(xq.z, va.z, fmaf(xq.w, va.w, pv[m0]))));
-            pv[m0 + 1] = fmaf(xq.x, vb.x, fmaf(xq.y, vb.y, fmaf(xq.z, vb.z, fmaf(xq.w, vb.w, pv[m0 + 1]))));
             release(rs, rph);
             if (++rs == nst) {
               rs = 0;
@@ -284,24 +288,26 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
       const uint32_t rph0 = rph;
       float sa = 0.f, sb = 0.f;
 #pragma unroll
-      for (int k = 0; k < NPT / 2; ++k) {
+      for (int k = 0; k < NGC; ++k) {
         if (k <= klg) {
           ok = tc::mbar_wait(&full[rs], rph, V2_WAIT_NS) && ok;
-          const float4* ch = ring + (size_t)rs * V2_CH4;  // float4 columns k CH4 + t and k CH4 + t + CONS
-          const int m0 = 2 * k, c40 = t + V2_CONS * m0, c41 = c40 + V2_CONS;
-          float4 v0 = ch[t], v1 = ch[t + V2_CONS];
-          if (k == klg) {
-            if (c40 >= n4) v0 = z4;
-            if (c41 >= n4) v1 = z4;
+          const float4* ch = ring + (size_t)rs * V2_CH4;
+#pragma unroll
+          for (int h = 0; h < V2_CW; ++h) {
+            const int m = V2_CW * k + h;
+            if (m < NPT) {
+              const int c4 = t + V2_CONS * m;
+              float4 v = ch[t + V2_CONS * h];
+              if (k == klg && c4 >= n4) v = z4;
+              if (h & 1) {
+                sb = fmaf(v.x, xv[4 * m], sb); sb = fmaf(v.y, xv[4 * m + 1], sb);
+                sb = fmaf(v.z, xv[4 * m + 2], sb); sb = fmaf(v.w, xv[4 * m + 3], sb);
+              } else {
+                sa = fmaf(v.x, xv[4 * m], sa); sa = fmaf(v.y, xv[4 * m + 1], sa);
+                sa = fmaf(v.z, xv[4 * m + 2], sa); sa = fmaf(v.w, xv[4 * m + 3], sa);
+              }
+            }
           }
-          sa = fmaf(v0.x, xv[4 * m0], sa);
-          sb = fmaf(v1.x, xv[4 * m0 + 4], sb);
-          sa = fmaf(v0.y, xv[4 * m0 + 1], sa);
-          sb = fmaf(v1.y, xv[4 * m0 + 5], sb);
-          sa = fmaf(v0.z, xv[4 * m0 + 2], sa);
-          sb = fmaf(v1.z, xv[4 * m0 + 6], sb);
-          sa = fmaf(v0.w, xv[4 * m0 + 3], sa);
-          sb = fmaf(v1.w, xv[4 * m0 + 7], sb);
           if (++rs == nst) {
             rs = 0;
             rph ^= 1u;
@@ -324,13 +330,13 @@ __global__ void __launch_bounds__(V2_THREADS, 1) k_v2_pass(V2Args a) {
       int us = rs0;
       uint32_t uph = rph0;
 #pragma unroll
-      for (int k = 0; k < NPT / 2; ++k) {
+      for (int k = 0; k < NGC; ++k) {
         if (k <= klg) {
           const float4* ch = ring + (size_t)us * V2_CH4;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int m = 2 * k + h, c4 = t + V2_CONS * m;
-            if (k < klg || c4 < n4) {
+          for (int h = 0; h < V2_CW; ++h) {
+            const int m = V2_CW * k + h, c4 = t + V2_CONS * m;
+            if (m < NPT && (k < klg || c4 < n4)) {
               const float4 gv = ch[t + V2_CONS * h];
               pv[4 * m + 0] = fmaf(w, gv.x, pv[4 * m + 0]);
               pv[4 * m + 1] = fmaf(w, gv.y, pv[4 * m + 1]);
