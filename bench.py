@@ -18,7 +18,8 @@ its inner FGM loop, stopping certificates and FP64 residuals.
 
 Other workloads: --workload small (n=50 FP64 DFGM), uneven (10000 mixed QPs,
 one persistent launch), mpc (16384 shared-matrix QPs), served (Poisson stream),
-sweep (the paper's eps_in sensitivity and outer-iteration-count studies).
+sweep (the paper's eps_in sensitivity and outer-iteration-count studies), sparse
+(one CSR QP, n = 2e6, p = 1e6).
 Multi-GPU: replicas only (independent instances per rank, no collectives).
 """
 from __future__ import annotations
@@ -41,7 +42,7 @@ METRIC = "QP solves/s at eps=1e-3"
 # capture (k_v2_pass at n = 12000, k_rows at n = 8192), applied to the full-size launches: both
 # kernels read every matrix element once, so traffic grows in proportion to the bytes a launch
 # processes
-TRAFFIC_RATIO = {"k_v2_pass": 1.0055, "k_rows": 1.0115}
+TRAFFIC_RATIO = {"k_v2_pass": 1.0068, "k_rows": 1.0115}
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -589,6 +590,89 @@ def run_sweep(args):
     ctx.close()
 
 
+def run_sparse(args):
+    """One large sparse QP in CSR form (Sec. 5's sparse case): n = 2e6, p = 1e6, Q a random-graph
+    Laplacian + diag (about 9 nonzeros per row), G with 8 per row; FP32 ADFGM, eps = 1e-3, last
+    iterate and average.  A step is one solve on the device-resident handle with the Lanczos
+    constants recomputed; e2e adds handle creation from host CSR arrays and the download."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    import workloads as W
+    from paper_1504_05708_gb300 import duquad as D
+    n, p = args.n, args.p
+    d = W.sparse_qp(n=n, p=p, seed=6)
+    stream = torch.cuda.current_stream()
+    ctx = D.Context(0, stream)
+
+    def make():
+        return D.SparseProblem(ctx, (d["Q_rowptr"], d["Q_col"], d["Q_val"]), d["q"],
+                               (d["G_rowptr"], d["G_col"], d["G_val"]), d["g"], d["lb"], d["ub"], prec=D.FP32,
+                               lmin_Q=d["lmin_Q"])
+    P = make()
+    o = D.opts(args.alg, eps_out=args.eps, eps_in=args.eps_in, check_every=args.check_every,
+               inner_check_every=args.inner_check_every, max_outer=20000, fresh_constants=1)
+    outs = (torch.empty(n, device="cuda"), torch.empty(n, device="cuda"), torch.empty(p, device="cuda"))
+    ms, clk, st, res = _timed(ctx, stream, lambda: P.solve(o, device_out=outs)[0], args.steps, args.warmup)
+    ctx.profile(True)
+    ctx.stats(reset=True)
+    r = P.solve(o, device_out=outs)[0]
+    torch.cuda.synchronize()
+    pst = ctx.stats(reset=True)
+    ctx.profile(False)
+    r = res[-1]
+    e2e = None
+    if not args.no_e2e:  # host CSR arrays through the ABI: create (validate, G', upload), solve, download
+        Pw = make()
+        Pw.solve(o)
+        Pw.close()
+        t0 = time.perf_counter()
+        for _ in range(max(1, min(args.steps, 2))):
+            Pe = make()
+            Pe.solve(o)
+            Pe.close()
+        e2e_s = (time.perf_counter() - t0) / max(1, min(args.steps, 2))
+        nnz = d["Q_col"].size + d["G_col"].size
+        e2e = {"value": 1.0 / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 12 * nnz + 4 * (n + p + 2) + 8 * (3 * n + p),
+               "d2h_bytes_per_step": 8 * (2 * n + p)}
+    peaks, kind = load_peaks()
+    achieved = pst["gemv_bytes"] / (pst["gemv_ms"] / 1e3) / 1e9 if pst["gemv_ms"] > 0 else None
+    # CPU baseline: the oracle's FOM step (FP64, scipy.sparse products) on the same data, scaled
+    import scipy.sparse as sp
+    Q = sp.csr_matrix((d["Q_val"], d["Q_col"], d["Q_rowptr"]), shape=(n, n))
+    G = sp.csr_matrix((d["G_val"], d["G_col"], d["G_rowptr"]), shape=(p, n))
+    y = np.zeros(n)
+    t0, k = time.perf_counter(), 0
+    while time.perf_counter() - t0 < min(args.cpu_seconds, 10.0):
+        y = O.sampled_fom_step(q=d["q"], g=d["g"], G=G, Q_rows=None, rows=None, y=y, mu=np.zeros(p), rho=0.3,
+                               L=40.0, lb=d["lb"], ub=d["ub"], Qy_full=Q @ y)
+        k += 1
+    per = (time.perf_counter() - t0) / k
+    line = _base_line(args, args.steps / (ms / 1e3), ms, f"sparse_csr_n{n}_p{p}_fp32_{args.alg.lower()}", "f32",
+                      {"n": n, "p": p, "nnz_Q": int(d["Q_col"].size), "nnz_G": int(d["G_col"].size),
+                       "alg": args.alg, "eps": args.eps, "eps_in": args.eps_in, "outputs": "last+average",
+                       "l2": "inputs larger than L2 (CSR arrays 0.3 GB)"}, clk, st, {
+                          "solve": {"status": r.status, "outer_iters": r.outer_iters, "inner_iters": r.inner_iters,
+                                    "f_last": r.f_last, "infeas_last": r.infeas_last, "f_avg": r.f_avg,
+                                    "infeas_avg": r.infeas_avg, "d_lb": r.d_lb,
+                                    "converged_last": r.converged_last, "converged_avg": r.converged_avg},
+                          "roofline": {"kernel": "k_csr_form + k_csr_rows (CSR products of the inner iteration)",
+                                       "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                       "frac": achieved / peaks["hbm_gbs"] if achieved else None, "traffic": None,
+                                       "peak_kind": kind, "launches_timed": pst["gemv_launches"],
+                                       "share_of_step": pst["gemv_ms"] / (ms / args.steps)},
+                          "e2e": e2e,
+                          "cpu_baseline": {"value": 1.0 / (per * max(r.inner_iters, 1)), "unit": "solves/s", "cores": 1,
+                                           "kind": "oracle",
+                                           "sample": f"{k} FOM steps of the oracle (FP64, scipy.sparse products) on the "
+                                                     f"same instance ({per:.3f} s each), scaled by the GPU run's "
+                                                     f"{r.inner_iters} inner iterations"}})
+    print(json.dumps(line), flush=True)
+    P.close()
+    ctx.close()
+
+
 UNEVEN_MAX_OUTER = 50000
 
 
@@ -868,7 +952,7 @@ def run_served(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="large", choices=["large", "eq", "small", "uneven", "mpc", "served",
-                                                             "sweep"])
+                                                             "sweep", "sparse"])
     ap.add_argument("--out", default="gpurun_out/sweep.json", help="sweep workload: where the table goes")
     ap.add_argument("--count", type=int, default=None)
     ap.add_argument("--rate", type=float, default=20000.0)
@@ -908,6 +992,10 @@ def main():
         run_served(args)
     elif args.workload == "sweep":
         run_sweep(args)
+    elif args.workload == "sparse":
+        if args.n == 20000 and args.p == 10000:  # the dense defaults: take the sparse case's sizes
+            args.n, args.p = 2_000_000, 1_000_000
+        run_sparse(args)
     else:
         run_gpu(args)
 

@@ -203,6 +203,41 @@ dq_status dq_context_destroy(dq_context *ctx);
  * with a message.  Errors: DQ_ERR_NOMEM, DQ_ERR_CUDA. */
 dq_status dq_problem_create(dq_context *ctx, const dq_problem_desc *desc, dq_problem **out);
 
+/* Sparse problems (CSR).  When Q and G are sparse, every step of the method
+ * is still a matrix-vector product and costs O(nnz) instead of O(n^2)
+ * (Sec. 5, the remark on sparse QPs).  Q is given as the full symmetric n x n
+ * matrix (both triangles), G as p x n, each in CSR: row offsets rowptr[rows+1]
+ * (rowptr[0] = 0, rowptr[rows] = nnz), column indices strictly increasing
+ * within a row, values; offsets and indices are int32 (nnz < 2^31).
+ * memory = DQ_HOST: values and vectors are doubles; DQ_DEVICE: every array is
+ * a device array (values and vectors of the precision's element type), copied
+ * to the host once for validation and for building G'.  prec: DQ_FP64 or
+ * DQ_FP32; one instance (batch 1), solved by the grid engine (DQ_ENGINE_AUTO
+ * or DQ_ENGINE_GRID; other engines return DQ_ERR_INVALID).  The library
+ * copies everything (nothing is borrowed).  Validation: consistent offsets,
+ * columns in range and increasing, finite values, lb <= ub, Q symmetric in
+ * structure and values (|Q_ij - Q_ji| <= tol sqrt(|Q_ii Q_jj|), tol as for
+ * dense problems); else DQ_ERR_INVALID.  G' is built on the host by a stable
+ * counting sort, so every product sums in a fixed order.  lipschitz:
+ * DQ_LIP_LANCZOS (Lanczos on the CSR products) or DQ_LIP_BOUND (the bounds of
+ * dq_lipschitz, computed from the CSR arrays in FP64 on the host). */
+typedef struct {
+  int32_t n, p;
+  int32_t cone;            /* dq_cone                                          */
+  int32_t prec;            /* DQ_FP64 or DQ_FP32                               */
+  int32_t memory;          /* dq_memory of every array below                   */
+  int32_t nnz_Q, nnz_G;
+  const int32_t *Q_rowptr, *Q_col;
+  const void *Q_val;
+  const int32_t *G_rowptr, *G_col;
+  const void *G_val;
+  const void *q, *g, *lb, *ub;
+  double lmax_Q, lmin_Q, normG2; /* as in dq_problem_desc                      */
+  int32_t lipschitz;       /* dq_lipschitz                                     */
+} dq_sparse_desc;
+
+dq_status dq_problem_create_sparse(dq_context *ctx, const dq_sparse_desc *desc, dq_problem **out);
+
 /* Replace q and/or g (NULL keeps the current one) of all `batch` instances;
  * arrays as in dq_problem_desc with the given memory kind. */
 dq_status dq_problem_set_vectors(dq_problem *prob, const void *q, const void *g, int32_t memory);

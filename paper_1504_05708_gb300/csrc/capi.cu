@@ -663,7 +663,8 @@ dq_status dq_problem_destroy(dq_problem* P) {
   cudaStreamSynchronize(P->ctx->stream);
   if (P->own_Q && P->Q) cudaFree(P->Q);
   if (P->own_G && P->G) cudaFree(P->G);
-  void* bufs[] = {P->GT, P->q, P->g, P->lb, P->ub, P->x_state, P->lam_state};
+  void* bufs[] = {P->GT, P->q, P->g, P->lb, P->ub, P->x_state, P->lam_state,
+                  P->q_rp, P->q_ci, P->g_rp, P->g_ci, P->gt_rp, P->gt_ci};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->gws) grid_free(P->gws);
@@ -688,6 +689,13 @@ dq_status dq_solve(dq_problem* P, const dq_solve_opts* o, const dq_outputs* out,
   }
   DQ_CK(cudaSetDevice(P->ctx->device));
   int engine = c.engine;
+  if (P->sparse) {  // CSR problems run on the grid engine's sparse products
+    if (engine != DQ_ENGINE_AUTO && engine != DQ_ENGINE_GRID) {
+      set_error("sparse (CSR) problems run on the grid engine");
+      return DQ_ERR_INVALID;
+    }
+    return grid_solve(P, c, out, results);
+  }
   if (engine == DQ_ENGINE_AUTO) {
     if (P->prec == DQ_BF16X3) engine = DQ_ENGINE_TC;
     else if (P->batch == 1 && P->n > 1024) engine = DQ_ENGINE_GRID;

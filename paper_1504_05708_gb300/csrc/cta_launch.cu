@@ -285,6 +285,11 @@ static dq_status run(dq_problem* const* probs, int count, const SolveCfg* cfgs, 
 dq_status cta_solve_problems(dq_problem* const* probs, int count, const SolveCfg* cfgs,
                              const dq_outputs* outs, dq_result* results, int smem_cap, int threads,
                              bool graph) {
+  for (int i = 0; i < count; ++i)
+    if (probs[i]->sparse) {
+      set_error("problem %d is sparse (CSR): sparse problems run on the grid engine (dq_solve)", i);
+      return DQ_ERR_INVALID;
+    }
   if (probs[0]->prec == DQ_FP64)
     return run<double>(probs, count, cfgs, outs, results, smem_cap, threads, graph);
   return run<float>(probs, count, cfgs, outs, results, smem_cap, threads, graph);

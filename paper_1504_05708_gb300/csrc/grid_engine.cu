@@ -1168,7 +1168,9 @@ struct GridRun {
           J.M1 = GT(); J.R1 = n; J.cols = p; J.out1 = v(W->tn);
           J.vmode = VM_W; J.a0 = v(GX[sx]); J.a1 = v(GX[sxp]); J.a2 = mu; J.a3 = g();
           J.beta = T(beta); J.rho = T(rho); J.done = dn;
-          const double bw = double(sizeof(T)) * (double(n) * p + 4.0 * p + n);
+          // matrix bytes: dense G', or CSR values + column indices + row offsets
+          const double mw = P->sparse ? double(P->nnzG) * (sizeof(T) + 4) + 4.0 * (n + 1) : double(sizeof(T)) * n * p;
+          const double bw = mw + double(sizeof(T)) * (4.0 * p + n);
           if ((e = timed(J, k, bw)) != cudaSuccess) break;
         }
         // x^k = [y - grad/L]_U in the prologue; then Q x^k (and G x^k)
@@ -1178,8 +1180,10 @@ struct GridRun {
         J.vmode = VM_STEP; J.a0 = v(X[sx]); J.a1 = v(X[sxp]); J.a2 = v(QX[sx]); J.a3 = v(QX[sxp]);
         J.a4 = aug ? q() : v(W->c); J.a5 = aug ? v(W->tn) : nullptr; J.a6 = lb(); J.a7 = ub();
         J.beta = T(beta); J.L = T(LL); J.vout = v(X[sn]); J.done = dn;
-        const double bx = double(sizeof(T)) * (double(n) * n + (aug ? double(p) * n : 0.0) +
-                                               (aug ? 10.0 : 9.0) * n + (aug ? p : 0));
+        const double mx = P->sparse ? double(P->nnzQ + (aug ? P->nnzG : 0)) * (sizeof(T) + 4) +
+                                          4.0 * (n + 1 + (aug ? p + 1 : 0))
+                                    : double(sizeof(T)) * (double(n) * n + (aug ? double(p) * n : 0.0));
+        const double bx = mx + double(sizeof(T)) * ((aug ? 10.0 : 9.0) * n + (aug ? p : 0));
         if ((e = timed(J, k, bx)) != cudaSuccess) break;
         beta = next_beta();
       }

@@ -418,8 +418,8 @@ dq_status dq_submit(dq_context* ctx, dq_problem* prob, const dq_solve_opts* opts
     return DQ_ERR_INVALID;
   }
   ServeState* S = ctx->serve;
-  if (prob->ctx != ctx || prob->prec != DQ_FP32 || prob->batch != 1) {
-    set_error("served problems are single FP32 instances of this context");
+  if (prob->ctx != ctx || prob->prec != DQ_FP32 || prob->batch != 1 || prob->sparse) {
+    set_error("served problems are single dense FP32 instances of this context");
     return DQ_ERR_INVALID;
   }
   if (prob->n > S->nmax || prob->p > S->pmax || prob_bytes(prob) > S->budget) {

@@ -41,6 +41,16 @@ class ProblemDesc(ctypes.Structure):
                 ("lipschitz", ctypes.c_int32)]
 
 
+class SparseDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("p", ctypes.c_int32), ("cone", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("memory", ctypes.c_int32), ("nnz_Q", ctypes.c_int32), ("nnz_G", ctypes.c_int32),
+                ("Q_rowptr", ctypes.c_void_p), ("Q_col", ctypes.c_void_p), ("Q_val", ctypes.c_void_p),
+                ("G_rowptr", ctypes.c_void_p), ("G_col", ctypes.c_void_p), ("G_val", ctypes.c_void_p),
+                ("q", ctypes.c_void_p), ("g", ctypes.c_void_p), ("lb", ctypes.c_void_p), ("ub", ctypes.c_void_p),
+                ("lmax_Q", ctypes.c_double), ("lmin_Q", ctypes.c_double), ("normG2", ctypes.c_double),
+                ("lipschitz", ctypes.c_int32)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("alg", ctypes.c_int32), ("output", ctypes.c_int32), ("inner_stop", ctypes.c_int32),
                 ("engine", ctypes.c_int32), ("eps_out", ctypes.c_double), ("eps_in", ctypes.c_double),
@@ -99,7 +109,7 @@ SYMBOLS = ("dq_context_create", "dq_context_destroy", "dq_problem_create", "dq_p
            "dq_problem_constants", "dq_problem_destroy", "dq_solve", "dq_solve_many", "dq_serve_start",
            "dq_submit", "dq_poll", "dq_serve_stop", "dq_context_profile", "dq_context_stats",
            "dq_autotune", "dq_solve_noalloc", "dq_test_tc_gemm", "dq_test_bounded_wait", "dq_theory",
-           "dq_solve_theory", "dq_last_error", "dq_version")
+           "dq_solve_theory", "dq_problem_create_sparse", "dq_last_error", "dq_version")
 
 _lib = None
 
@@ -145,6 +155,7 @@ def lib(build_if_needed: bool = True):
     L.dq_context_profile.argtypes = [vp, ctypes.c_int32]
     L.dq_context_stats.argtypes = [vp, P(Stats), ctypes.c_int32]
     L.dq_theory.argtypes = [P(TheoryIn), P(TheoryOut)]
+    L.dq_problem_create_sparse.argtypes = [vp, P(SparseDesc), P(vp)]
     L.dq_solve_theory.argtypes = [vp, P(TheorySolveOpts), P(Outputs), P(Result), P(TheoryOut),
                                   P(ctypes.c_double)]
     for name in SYMBOLS[:-2]:
@@ -347,6 +358,52 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def _iptr(a):
+    """Host numpy (int32, C-contiguous) or torch int32 tensor -> (pointer, keepalive)."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=np.int32)
+    return arr.ctypes.data, arr
+
+
+class SparseProblem(Problem):
+    """A sparse QP (dq_problem_create_sparse): Q (full symmetric) and G as CSR triples
+    (rowptr, col, val).  Host: numpy (int32 indices, values converted to double); device:
+    torch CUDA tensors (int32 indices, values of the precision's dtype)."""
+
+    def __init__(self, ctx: Context, Qcsr, q, Gcsr, g, lb, ub, *, prec=FP32, cone=CONE_INEQ, lmax_Q=NAN,
+                 lmin_Q=NAN, normG2=NAN, lipschitz=LIP_LANCZOS):
+        self.ctx = ctx
+        dev = hasattr(q, "data_ptr") and getattr(q, "is_cuda", False)
+        n = int(q.shape[-1])
+        p = int(g.shape[-1]) if g is not None else 0
+        d = SparseDesc()
+        d.n, d.p, d.cone, d.prec, d.memory = n, p, cone, prec, DEVICE if dev else HOST
+        keep = []
+        for name, (rp, ci, va) in (("Q", Qcsr), ("G", Gcsr if p else (None, None, None))):
+            if rp is None:
+                continue
+            prp, k1 = _iptr(rp)
+            pci, k2 = _iptr(ci)
+            pva, k3 = _ptr(va)
+            keep += [k1, k2, k3]
+            setattr(d, name + "_rowptr", prp)
+            setattr(d, name + "_col", pci)
+            setattr(d, name + "_val", pva)
+            setattr(d, "nnz_" + name, int(ci.shape[0]))
+        for f, a in (("q", q), ("g", g), ("lb", lb), ("ub", ub)):
+            ptr, k = _ptr(a)
+            keep.append(k)
+            setattr(d, f, ptr)
+        d.lmax_Q, d.lmin_Q, d.normG2 = lmax_Q, lmin_Q, normG2
+        d.lipschitz = lipschitz
+        h = ctypes.c_void_p()
+        check(lib().dq_problem_create_sparse(ctx.h, ctypes.byref(d), ctypes.byref(h)), (OK,))
+        self.h = h
+        self.n, self.p, self.batch, self.prec = n, p, 1, prec
+        self._borrowed = None
 
 
 def autotune(problems, o_list, sample=256):

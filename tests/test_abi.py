@@ -60,7 +60,8 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     from paper_1504_05708_gb300 import duquad as D
     pairs = {"dq_problem_desc": D.ProblemDesc, "dq_solve_opts": D.SolveOpts, "dq_result": D.Result,
              "dq_outputs": D.Outputs, "dq_stats": D.Stats, "dq_theory_in": D.TheoryIn,
-             "dq_theory_out": D.TheoryOut, "dq_theory_solve_opts": D.TheorySolveOpts}
+             "dq_theory_out": D.TheoryOut, "dq_theory_solve_opts": D.TheorySolveOpts,
+             "dq_sparse_desc": D.SparseDesc}
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "duquad.h"', "int main(void) {"]
     for cname, py in pairs.items():
         lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')

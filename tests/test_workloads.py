@@ -115,3 +115,26 @@ def test_hidden_top_eigenvectors_are_orthogonal_to_ones():
     assert abs(eg[-1] - 9.0) <= 1e-9 and eg[-2] <= 1.0 + 1e-12
     assert abs(abs(V[:, -1] @ v) - 1.0) <= 1e-12
     assert inst.lmin_Q <= ev[0] and ev[0] >= 1.0 - 1e-9
+
+
+def test_sparse_qp_is_valid_csr_and_symmetric_pd():
+    """The sparse generator: valid CSR (offsets, strictly increasing columns), Q symmetric with
+    lambda_min(Q) >= 1 (Laplacian + diag >= 1), G with row_nnz distinct columns per row, and the
+    dense expansion equal to the CSR arrays."""
+    d = W.sparse_qp(n=300, p=120, deg=8, row_nnz=8, seed=3, dense=True)
+    n, p = 300, 120
+    for pre, rows in (("Q", n), ("G", p)):
+        rp, ci = d[pre + "_rowptr"], d[pre + "_col"]
+        assert rp.dtype == np.int32 and ci.dtype == np.int32 and rp[0] == 0 and rp[-1] == ci.size
+        for r in range(rows):
+            c = ci[rp[r]:rp[r + 1]]
+            assert np.all(np.diff(c) > 0) and c.min() >= 0 and c.max() < n
+    Q, G = d["Q"], d["G"]
+    assert np.array_equal(Q, Q.T)
+    assert np.linalg.eigvalsh(Q)[0] >= 1.0 - 1e-9
+    assert np.all(np.diff(d["G_rowptr"]) == 8) and np.count_nonzero(G) == p * 8
+    x = np.random.default_rng(0).standard_normal(n)
+    Qx = np.array([d["Q_val"][d["Q_rowptr"][r]:d["Q_rowptr"][r + 1]] @ x[d["Q_col"][d["Q_rowptr"][r]:d["Q_rowptr"][r + 1]]]
+                   for r in range(n)])
+    np.testing.assert_allclose(Qx, Q @ x, rtol=1e-12, atol=1e-12)
+    assert np.all(d["g"] <= -0.1)

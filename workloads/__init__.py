@@ -292,3 +292,67 @@ def hidden_top(n=200, p=80, seed=0, lam_lo=1.0, lam_hi=100.0, lam_top=200.0, s_t
     ev = np.linalg.eigvalsh(Q)
     return Instance(Q, q, G, g, -np.ones(n), np.ones(n), float(ev[0]) * (1 - 1e-9), float(ev[-1]), "ADFGM",
                     {"kind": "hidden_top", "seed": seed})
+
+
+def sparse_qp(n=100000, p=50000, deg=8, row_nnz=8, seed=6, dense=False):
+    """Sparse QP in CSR form (the sparse case of Sec. 5, e.g. network utility maximisation).
+
+    Q = L + diag(d): L the Laplacian of a random graph with about n deg / 2 edges (each node
+    draws deg / 2 neighbours uniformly; weights ~ U[0.5, 1.5], repeated edges summed) and
+    d ~ U[1, 10], so Q is symmetric with lambda_min(Q) >= 1 (L is PSD) and about (deg + 1) n
+    nonzeros.  G is p x n with row_nnz distinct uniform columns per row, values N(0, 1/row_nnz);
+    q ~ N(0,1); g = -|N(0,1)| - 0.1 (x = 0 strictly feasible); box [-1, 1].
+    Returns a dict of numpy arrays: Q_rowptr, Q_col, Q_val, G_rowptr, G_col, G_val (int32
+    indices, float64 values), q, g, lb, ub, lmin_Q = 1.0; dense=True adds Q and G as dense
+    arrays (small n only)."""
+    rng = np.random.default_rng(seed)
+    half = max(deg // 2, 1)
+    src = np.repeat(np.arange(n, dtype=np.int64), half)
+    dst = rng.integers(0, n, src.size)
+    keep = src != dst
+    i, j = np.minimum(src[keep], dst[keep]), np.maximum(src[keep], dst[keep])
+    w = rng.uniform(0.5, 1.5, i.size)
+    key = i * n + j
+    uk, inv = np.unique(key, return_inverse=True)
+    wu = np.bincount(inv, weights=w)
+    ei, ej = uk // n, uk % n
+    d = rng.uniform(1.0, 10.0, n)
+    diag = d + np.bincount(ei, weights=wu, minlength=n) + np.bincount(ej, weights=wu, minlength=n)
+    rows = np.concatenate([np.arange(n), ei, ej])
+    cols = np.concatenate([np.arange(n), ej, ei])
+    vals = np.concatenate([diag, -wu, -wu])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    Q_rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(Q_rowptr, rows + 1, 1)
+    Q_rowptr = np.cumsum(Q_rowptr).astype(np.int32)
+    # G: row_nnz distinct columns per row (sorted)
+    k = min(row_nnz, n)
+    G_col = _distinct_cols(rng, p, n, k).reshape(-1).astype(np.int32)
+    G_val = rng.standard_normal(p * k) / np.sqrt(k)
+    G_rowptr = (np.arange(p + 1) * k).astype(np.int32)
+    q = rng.standard_normal(n)
+    g = -np.abs(rng.standard_normal(p)) - 0.1
+    out = dict(n=n, p=p, Q_rowptr=Q_rowptr, Q_col=cols.astype(np.int32), Q_val=vals, G_rowptr=G_rowptr,
+               G_col=G_col, G_val=G_val, q=q, g=g, lb=-np.ones(n), ub=np.ones(n), lmin_Q=1.0)
+    if dense:
+        Q = np.zeros((n, n))
+        Q[rows, cols] = vals
+        G = np.zeros((p, n))
+        G[np.repeat(np.arange(p), k), G_col] = G_val
+        out["Q"], out["G"] = Q, G
+    return out
+
+
+def _distinct_cols(rng, p, n, k):
+    """p rows of k distinct column indices in [0, n) (rejection of repeats, row by row)."""
+    c = rng.integers(0, n, (p, k))
+    for _ in range(64):
+        s = np.sort(c, axis=1)
+        dup = np.zeros_like(c, dtype=bool)
+        dup[:, 1:] = s[:, 1:] == s[:, :-1]
+        if not dup.any():
+            return s
+        s[dup] = rng.integers(0, n, int(dup.sum()))
+        c = s
+    raise RuntimeError("could not draw distinct columns")
