@@ -11,6 +11,8 @@
 // butterfly order, so the result depends on the row's structure only (not on
 // the grid or on which rows share a warp).
 #pragma once
+#include <type_traits>
+
 #include "dq_common.cuh"
 
 namespace dq {
@@ -31,33 +33,39 @@ __global__ void __launch_bounds__(256) k_csr_rows(Job J, CsrRef A1, CsrRef A2, c
   const int groups = (gridDim.x * blockDim.x) / TPR;
   const int g0 = (gtid - lane) / TPR, gi = lane / TPR;  // the warp's first group, this lane's group
   const int R = J.R1 + J.R2;
+  // accurate mode: Dot2 per lane and FP64 lane sums; otherwise the row is
+  // summed in T (FP64 arithmetic runs at a small fraction of the FP32 rate)
+  using S = typename std::conditional<ACC, double, T>::type;
   for (int base = g0; base < R; base += groups) {  // the same trips for every lane of the warp
     const int r = base + gi;
-    double tot = 0.0;
+    S tot = S(0);
     if (r < R) {
       const bool first = r < J.R1;
       const CsrRef A = first ? A1 : A2;
       const T* M = first ? J.M1 : J.M2;
       const int row = first ? r : r - J.R1;
       const int e0 = __ldg(A.rp + row), e1 = __ldg(A.rp + row + 1);
-      if (ACC) {
+      if constexpr (ACC) {
         typename AccurateAcc<T>::type a;
         for (int e = e0 + sub; e < e1; e += TPR) a.add(__ldcs(M + e), __ldg(v + __ldcs(A.ci + e)));
         tot = a.get();
       } else {
-        T s = T(0);
-        for (int e = e0 + sub; e < e1; e += TPR) s = fma(__ldcs(M + e), __ldg(v + __ldcs(A.ci + e)), s);
-        tot = double(s);
+        for (int e = e0 + sub; e < e1; e += TPR) tot = fma(__ldcs(M + e), __ldg(v + __ldcs(A.ci + e)), tot);
       }
     }
 #pragma unroll
     for (int o = TPR / 2; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (r < R && sub == 0) {
       if (r < J.R1) {
-        if (J.add1) tot += double(J.add1[r]);
-        if (ACC) J.dout1[r] = tot; else J.out1[r] = T(tot);
+        if constexpr (ACC) {
+          double d = tot;
+          if (J.add1) d += double(J.add1[r]);
+          J.dout1[r] = d;
+        } else {
+          J.out1[r] = J.add1 ? tot + J.add1[r] : tot;
+        }
       } else {
-        if (ACC) J.dout2[r - J.R1] = tot; else J.out2[r - J.R1] = T(tot);
+        if constexpr (ACC) J.dout2[r - J.R1] = tot; else J.out2[r - J.R1] = tot;
       }
     }
   }

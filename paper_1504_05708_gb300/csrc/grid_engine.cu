@@ -747,7 +747,9 @@ struct GridRun {
     const long long nnz = (long long)((A1.rp == P->q_rp) ? P->nnzQ : (A1.rp == P->g_rp ? P->nnzG : P->nnzG)) +
                           (J.M2 ? P->nnzG : 0);
     const double avg = double(nnz) / std::max(1, J.R1 + J.R2);
-    const int tpr = avg > 24 ? 32 : avg > 12 ? 16 : avg > 6 ? 8 : avg > 3 ? 4 : 2;
+    // about two entries per lane: fewer lanes per row than entries keeps the
+    // shuffle tree short and the lanes busy
+    const int tpr = avg >= 48 ? 32 : avg >= 24 ? 16 : avg >= 12 ? 8 : avg >= 6 ? 4 : 2;
     switch (tpr) {
       case 32: csr_launch<ACC, 32>(J, A1, A2, v); break;
       case 16: csr_launch<ACC, 16>(J, A1, A2, v); break;
