@@ -441,6 +441,16 @@ def run_small(args):
             torch.empty(25, dtype=torch.float64, device="cuda"))
     ms, clk, st, res = _timed(ctx, stream, lambda: P.solve(o, device_out=outs)[0], args.steps, args.warmup)
     r = res[-1]
+    # where a solve's time goes: the same solve with the handle's constants (no Lanczos runs),
+    # and one outer iteration of one inner iteration (launch, set-up, evaluation, copies)
+    o_keep = D.opts("DFGM", eps_out=1e-4, engine=D.ENGINE_CTA)
+    o_min = D.opts("DFGM", engine=D.ENGINE_CTA, fixed_outer=1, fixed_inner=1)
+    ms_keep = _timed(ctx, stream, lambda: P.solve(o_keep, device_out=outs)[0], args.steps, 2)[0] / args.steps
+    ms_min = _timed(ctx, stream, lambda: P.solve(o_min, device_out=outs)[0], args.steps, 2)[0] / args.steps
+    ms_solve = ms / args.steps
+    breakdown = {"solve_ms": ms_solve, "lanczos_ms": ms_solve - ms_keep,
+                 "iterations_ms": ms_keep - ms_min, "launch_setup_eval_ms": ms_min,
+                 "us_per_inner_iteration": 1e3 * (ms_keep - ms_min) / max(r.inner_iters - 1, 1)}
     # e2e: host arrays through the ABI (handle creation, upload, solve, download, destroy)
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -459,6 +469,7 @@ def run_small(args):
                       clk, st, {
                           "solve": {"status": r.status, "outer_iters": r.outer_iters, "inner_iters": r.inner_iters,
                                     "f_last": r.f_last, "infeas_last": r.infeas_last},
+                          "breakdown": breakdown,
                           "roofline": {"kernel": "cta_solve_kernel<double>", "bound": "alu",
                                        "achieved": flops / (ms / args.steps / 1e3) / 1e12, "peak": FP64_SM_TFLOPS,
                                        "unit": "TFLOP/s", "frac": flops / (ms / args.steps / 1e3) / 1e12 / FP64_SM_TFLOPS,

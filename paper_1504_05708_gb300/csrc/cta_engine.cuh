@@ -54,8 +54,11 @@ struct CtaInst {
 // out[i] = sum_j M[j*ld + i] v[j], i < cols, j < rows  (out = M' v).
 // Work units of one lane: cpw columns 32 apart (cpw = 4 for cols >= 128, 2 for
 // cols >= 64, else 1; a warp's load covers 128 contiguous bytes) over one of S
-// contiguous row segments, S chosen for about 512 units (S = 1 for products of
-// at most 4096 terms, where the split costs more than it saves).  A unit walks its rows
+// contiguous row segments, S chosen for about 512 units (FP32: S = 1 for
+// products of at most 4096 terms, where the split costs more than it saves;
+// FP64: at least 256 units, because the FP64 pipe is slow and a long
+// dependent chain per lane left most warps waiting at the next barrier, e.g.
+// 64 lanes with 25 FMAs each at n = 50).  A unit walks its rows
 // four at a time (16 loads in flight for cpw = 4), even rows into one
 // accumulator and odd rows into another, and the S segment sums are added in
 // segment order in `part` (at most 2048 elements).  Every sum's order is fixed
@@ -68,8 +71,9 @@ __device__ __forceinline__ void mtv(const T* __restrict__ M, int rows, int cols,
   // columns of doubles would not stay in registers
   const int cpw = sizeof(T) == 8 ? 1 : (cols >= 128 ? 4 : (cols >= 64 ? 2 : 1));
   const int bw = 32 * cpw, units = ((cols + bw - 1) / bw) * 32;
-  // small products (a few thousand terms) skip the segment split and its barrier
-  const int S = (units >= 512 || (long long)rows * cols <= 4096) ? 1 : min(8, 512 / units);
+  // small FP32 products (a few thousand terms) skip the segment split and its barrier
+  const int S = sizeof(T) == 8 ? (units >= 256 ? 1 : min(8, 256 / units))
+                               : ((units >= 512 || (long long)rows * cols <= 4096) ? 1 : min(8, 512 / units));
   for (int q = threadIdx.x; q < S * units; q += blockDim.x) {
     const int sg = q / units, rem = q - sg * units;
     const int cbase = (rem >> 5) * bw + (rem & 31);
