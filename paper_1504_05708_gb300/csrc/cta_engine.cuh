@@ -501,9 +501,117 @@ __device__ inline void warp_tridiag_top(const double* a, const double* b, int m,
 // or theta + 2 r, whichever is larger).  Products in T, the three-term
 // recurrence and the tridiagonal eigenproblem in FP64.
 // Scratch: A.x, B.x, A.Qx, A.Gx, dn, usum.
+// The same Lanczos for FP32 instances with n, p <= 64, run by warp 0 alone
+// (the block waits once): at these sizes the block version spent most of
+// its time in the barriers of its block reductions (about nine per step).
+// Lane l holds rows l and l + 32 of v and w; a product out = M' v reads
+// column i of M (conflict-free in shared memory) with a sequential FP32 sum
+// over the rows, as the block version's products, and the dot products are
+// FP64 butterflies, so every sum has a fixed order.  Result in out[0].
+__device__ inline void warp_lanczos(const CtaInst<float>& I, CtaWs<float>& W, int which, double* out) {
+  const int n = I.n, p = I.p, lane = threadIdx.x & 31;
+  float* v = W.A.x;   // the current Lanczos vector (every product reads all of it)
+  float* t = W.A.Gx;  // G v (which = 1)
+  double* al = W.dn;
+  double* be = W.usum;
+  auto wsum = [](double x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  };
+  // out[i] = sum_j A[j * lda + i] x[j] over j < rows, this lane's i = l, l + 32
+  auto prod = [&](const float* A, int rows, int cols, int lda, const float* x, double (&o)[2]) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      float s = 0.f;
+      if (i < cols)
+        for (int j = 0; j < rows; ++j) s = fmaf(A[j * lda + i], x[j], s);
+      o[h] = double(s);
+    }
+  };
+  double vl[2], vpl[2] = {0.0, 0.0}, wl[2];
+  double ps = 0.0;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    vl[h] = i < n ? lz_start((unsigned long long)i) : 0.0;
+    ps += vl[h] * vl[h];
+  }
+  const double inv = 1.0 / sqrt(wsum(ps));
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+    vl[h] = i < n ? double(float(vl[h] * inv)) : 0.0;  // the vector the products see
+    if (i < n) v[i] = float(vl[h]);
+  }
+  __syncwarp();
+  const int ksteps = min(lz_min_steps(n), kLzMaxSteps);
+  double beta_prev = 0.0, theta = 0.0, r = 0.0;
+  bool exhausted = false;
+  for (int j = 0; j < ksteps; ++j) {
+    if (which == 0) {
+      prod(W.Q, n, n, n, v, wl);
+    } else {
+      double tl[2];
+      prod(W.GT, n, p, p, v, tl);  // t = G v (columns of G')
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (lane + 32 * h < p) t[lane + 32 * h] = float(tl[h]);
+      __syncwarp();
+      prod(W.G, p, n, n, t, wl);   // w = G' t
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) wl[h] = lane + 32 * h < n ? wl[h] : 0.0;
+    const double alpha = wsum(vl[0] * wl[0] + vl[1] * wl[1]);
+    double pb = 0.0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double rr = lane + 32 * h < n ? wl[h] - alpha * vl[h] - beta_prev * vpl[h] : 0.0;
+      wl[h] = rr;
+      pb += rr * rr;
+    }
+    const double beta = sqrt(wsum(pb));
+    if (lane == 0) {
+      al[j] = alpha;
+      be[j] = beta;
+    }
+    const bool invariant = !(beta > 1e-300);
+    if (invariant || j + 1 == ksteps) {
+      __syncwarp();
+      warp_tridiag_top(al, be, j + 1, W.red + 34);
+      __syncwarp();
+      theta = W.red[34];
+      r = beta * W.red[35];
+      exhausted = invariant || j + 1 == n;
+      break;
+    }
+    __syncwarp();  // every lane has read v in its products
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = lane + 32 * h;
+      vpl[h] = vl[h];
+      vl[h] = i < n ? double(float(wl[h] / beta)) : 0.0;
+      if (i < n) v[i] = float(vl[h]);
+    }
+    beta_prev = beta;
+    __syncwarp();
+  }
+  if (lane == 0) out[0] = lz_estimate(theta, r, exhausted, 6.0e-8);
+}
+
 template <typename T>
 __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int which) {
   const int n = I.n, p = I.p;
+  if constexpr (sizeof(T) == 4) {
+    if (n <= 64 && p <= 64) {
+      __syncthreads();
+      if (threadIdx.x < 32) warp_lanczos(I, W, which, W.red + 36);
+      __syncthreads();
+      const double est = W.red[36];
+      __syncthreads();
+      return est;
+    }
+  }
   T* v = W.A.x;
   T* vp = W.B.x;
   T* w = W.A.Qx;
