@@ -901,7 +901,10 @@ struct GridRun {
   }
 
   // ---- single-pass iteration (grid_v2.cuh): setup and launch
-  static constexpr double kV2GWeight = 0.8;  // best of a sweep at n = 20000, p = 10000 (0.6 .. 1.25)
+  // G bytes weigh this much against packed-Q bytes in the CTA split; best of a sweep with
+  // 32 KB stages (GB/s of k_v2_pass at n = 20000 / 12000): 0.8 6021 / 5487, 0.9 6347 / 5752,
+  // 1.0 6597 / 6060, 1.2 6322 / 5952
+  static constexpr double kV2GWeight = 1.0;
   static constexpr int kCertStride = 256;    // >= reduction blocks for n <= 20480
   bool use_v2 = false;
   int v2_nQ = 0, v2_nG = 0, v2_npt = 0;
