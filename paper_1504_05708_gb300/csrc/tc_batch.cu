@@ -863,6 +863,15 @@ void tc_free(TcWs* w) {
   delete w;
 }
 
+static size_t tc_smem_bytes(const TcWs* W) {
+  auto r128 = [](size_t b) { return (b + 127) & ~size_t(127); };
+  const size_t qb = (size_t)W->NPAD * W->NPAD * 2;
+  const size_t ab = std::max((size_t)TM * W->NPAD * 2, (size_t)2 * TM * TC_KC * 2);
+  const size_t bb = r128(std::max(std::max((size_t)W->NC * W->NPAD * 2, (size_t)W->NPAD * TC_KC * 2),
+                                  (size_t)W->NPAD * W->NPAD));
+  return 2 * r128(qb) + r128(2 * ab) + 4 * bb + 2 * r128((size_t)W->NPAD * 4) + 128;
+}
+
 static dq_status tc_ws(dq_problem* P, TcWs** out) {
   if (P->tws) {
     *out = P->tws;
@@ -871,7 +880,13 @@ static dq_status tc_ws(dq_problem* P, TcWs** out) {
   TcWs* W = new TcWs();
   const int n = P->n, p = P->p, B = P->batch;
   W->NPAD = (n + 15) / 16 * 16;
-  W->NC = std::min(64, W->NPAD);
+  // G rows per chunk of the G ubar product: as many as shared memory allows (at most
+  // NPAD, the accumulator slot's width): fewer chunks, each a bulk copy, an MMA and an
+  // epilogue on the serial chain of every outer iteration (112 at n = 100: 6 chunks
+  // instead of 10 for p = 600).  The chunking does not change any sum.
+  W->NC = W->NPAD;
+  const size_t smem_lim = max_dynamic_smem((const void*)k_tc_solve, P->ctx->smem_optin);
+  while (W->NC > 16 && tc_smem_bytes(W) > smem_lim) W->NC -= 16;
   W->ntiles = (B + TM - 1) / TM;
   W->nchG = (p + W->NC - 1) / W->NC;
   W->nchGT = (p + TC_KC - 1) / TC_KC;
@@ -911,14 +926,6 @@ static dq_status tc_ws(dq_problem* P, TcWs** out) {
   return DQ_OK;
 }
 
-static size_t tc_smem_bytes(const TcWs* W) {
-  auto r128 = [](size_t b) { return (b + 127) & ~size_t(127); };
-  const size_t qb = (size_t)W->NPAD * W->NPAD * 2;
-  const size_t ab = std::max((size_t)TM * W->NPAD * 2, (size_t)2 * TM * TC_KC * 2);
-  const size_t bb = r128(std::max(std::max((size_t)W->NC * W->NPAD * 2, (size_t)W->NPAD * TC_KC * 2),
-                                  (size_t)W->NPAD * W->NPAD));
-  return 2 * r128(qb) + r128(2 * ab) + 4 * bb + 2 * r128((size_t)W->NPAD * 4) + 128;
-}
 
 dq_status tc_solve(dq_problem* P, const SolveCfg& c, const dq_outputs* out, dq_result* results) {
   std::lock_guard<std::mutex> lk(P->mu);
