@@ -47,7 +47,7 @@ __global__ void k_pack_kmajor(const float* __restrict__ src, int R_valid, int K_
                               uint4* __restrict__ hi, uint4* __restrict__ lo);
 
 static constexpr int TM = 128;                        // instances per tile (TMEM lanes, threads)
-static constexpr int TC_KC = 48;                      // constraints per G' chunk (MMA K)
+static constexpr int TC_KC = 64;                      // constraints per G' chunk (MMA K; 48 took 13 chunks at p = 600)
 static constexpr unsigned long long kTcWaitNs = 2000000000ull;
 
 struct TcArgs {
