@@ -27,7 +27,8 @@
 // and the column partial sums never leave registers.  Each wait on a stage
 // and each release serve four float4 per thread: with 16 KB chunks (two per
 // thread) the loop control per byte was twice as large and the kernel ran at
-// 0.73 of the measured HBM bandwidth instead of 0.90 at n = 20000.  Each CTA writes one
+// 0.73 of the measured HBM bandwidth instead of 0.90 at n = 20000 (0.98 once the
+// Q-CTA / G-CTA split was re-tuned for this shape).  Each CTA writes one
 // partial vector; k_v2_reduce adds the partial vectors in a fixed order
 // (deterministic) and the row dots, and forms the next iterate x^{k+1} from
 // them, so a pass reads only x^k besides the matrices.  HBM bytes per
@@ -432,7 +433,8 @@ __device__ __forceinline__ float v2_step4(const V2Step& st, int c4, const float4
 // G-CTA vectors, so both sums load at once (Kahan sums in FP32); the group
 // sums are then added in group order: deterministic for a fixed grid split.
 // (1024-thread blocks with eight loads in flight ran at half the speed: one
-// block per SM and a second wave.)
+// block per SM and a second wave; all of a thread's loads in flight at once
+// ran at 12.9 against 10.6 us per launch at n = 20000.)
 // Warp 0 forms x^{k+1} at the block's columns and the block's partial sum of
 // the step certificate.
 static constexpr int V2R_COLS = 32, V2R_GROUPS = 16;
@@ -482,23 +484,31 @@ __global__ void __launch_bounds__(V2R_COLS* V2R_GROUPS) k_v2_reduce(const float4
   __syncthreads();
   const int w = threadIdx.x / V2R_COLS;
   if (w < 2 && c4 < n4) {  // thread (w, col) adds the ng groups of sum w in order (w = 1: G' w, or zero)
-    double r0 = 0, r1 = 0, r2 = 0, r3 = 0;
+    // compensated FP32 sums (TwoSum) of the groups' (sum, -error) pairs: FP64 adds run at a
+    // small fraction of the FP32 rate on this GPU and were a visible part of this kernel
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+    auto two_sum = [](float& sum, float& err, float v) {
+      const float t = sum + v, bb = t - sum;
+      err += (sum - (t - bb)) + (v - bb);
+      sum = t;
+    };
     if (w == 0 || tnout) {
       for (int q = w * ng; q < (w + 1) * ng; ++q) {
         const float4 h = sh[0][q][col], l = sh[1][q][col];
-        r0 += double(h.x) + double(l.x);
-        r1 += double(h.y) + double(l.y);
-        r2 += double(h.z) + double(l.z);
-        r3 += double(h.w) + double(l.w);
+        two_sum(s[0], c[0], h.x); two_sum(s[0], c[0], l.x);
+        two_sum(s[1], c[1], h.y); two_sum(s[1], c[1], l.y);
+        two_sum(s[2], c[2], h.z); two_sum(s[2], c[2], l.z);
+        two_sum(s[3], c[3], h.w); two_sum(s[3], c[3], l.w);
       }
     }
     float4 r;
     if (w == 0) {
       const float4 d = ((const float4*)dotQ)[c4];
-      r = make_float4(float(r0 + d.x), float(r1 + d.y), float(r2 + d.z), float(r3 + d.w));
+      two_sum(s[0], c[0], d.x); two_sum(s[1], c[1], d.y); two_sum(s[2], c[2], d.z); two_sum(s[3], c[3], d.w);
+      r = make_float4(s[0] + c[0], s[1] + c[1], s[2] + c[2], s[3] + c[3]);
       ((float4*)qxout)[c4] = r;
     } else {
-      r = make_float4(float(r0), float(r1), float(r2), float(r3));
+      r = make_float4(s[0] + c[0], s[1] + c[1], s[2] + c[2], s[3] + c[3]);
       if (tnout) ((float4*)tnout)[c4] = r;
     }
     sres[w][col] = r;
