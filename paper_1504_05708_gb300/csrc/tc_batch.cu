@@ -302,6 +302,9 @@ __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out,
   const TcArgs& A = *C.a;
   const int NPAD = C.NPAD, h8 = 8 * C.half;
   const float L = A.L;
+  // the step 1/L as a multiplier: a correctly rounded FP32 division is about ten
+  // instructions, and the epilogue takes 56 of them per thread per iteration at n = 100
+  const float invL = 1.0f / L;
   // y^0 = x^0; D = Q x^0
   C.region_copy(C.rY, C.rX);
   C.operand_from(C.rX);
@@ -339,7 +342,7 @@ __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out,
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const float yv = __uint_as_float(y[i]), xv = __uint_as_float(x[i]);
-        const float s = yv - (__uint_as_float(d[i]) + __uint_as_float(c[i])) / L;
+        const float s = yv - (__uint_as_float(d[i]) + __uint_as_float(c[i])) * invL;
         const float lo = C.lb[c0 + h8 + i], hi = C.ub[c0 + h8 + i];
         float xnew = s < lo ? lo : (s > hi ? hi : s);
         float ynew = xnew + beta * (xnew - xv);
@@ -375,7 +378,7 @@ __device__ __forceinline__ void tc_inner(TcCtx& C, bool active, float& cert_out,
         const float gd = __uint_as_float(d[i]) + __uint_as_float(c[i]), xv = __uint_as_float(x[i]);
         const float lo = C.lb[col], hi = C.ub[col];
         if (fgm_sigma) {
-          const float xp = fminf(fmaxf(xv - gd / L, lo), hi);
+          const float xp = fminf(fmaxf(xv - gd * invL, lo), hi);
           const float dd = xv - xp;
           kahan(cs, cc, gd * dd + (L * dd) * (L * dd) * kap);
         } else {
