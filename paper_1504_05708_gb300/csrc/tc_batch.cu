@@ -738,12 +738,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs a) {
           }
         }
         if (a.want_avg) {  // x_avg = usum / S, evaluated in region X
+          // one FP64 division per lane, then FP32 products (an FP64 division per element
+          // ran on the slow FP64 pipe)
+          const float invS = S > 0.0 ? (float)(1.0 / S) : 0.f;
           for (int c0 = 0; c0 < NPAD; c0 += 16) {
             uint32_t v[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const int col = c0 + h8 + i;
-              v[i] = __float_as_uint(col < n && S > 0.0 ? (float)(a.usum[im(tile, n, col, lane)] / S) : 0.f);
+              v[i] = __float_as_uint(col < n ? a.usum[im(tile, n, col, lane)] * invS : 0.f);
             }
             C.st8(C.rX, c0, v);
           }
@@ -763,7 +766,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_tc_solve(TcArgs a) {
               for (int i = 0; i < 16; ++i) us[i] = i0 + i < n ? __ldcg(a.usum + im(tile, n, i0 + i, lane)) : 0.f;
 #pragma unroll
               for (int i = 0; i < 16; ++i)
-                if (i0 + i < n) a.xaT[im(tile, n, i0 + i, lane)] = (float)(us[i] / S);
+                if (i0 + i < n) a.xaT[im(tile, n, i0 + i, lane)] = us[i] * invS;
             }
           }
         }
