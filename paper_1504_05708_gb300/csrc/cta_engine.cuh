@@ -60,8 +60,9 @@ struct CtaInst {
 // dependent chain per lane left most warps waiting at the next barrier, e.g.
 // 64 lanes with 25 FMAs each at n = 50).  A unit walks its rows
 // four at a time (16 loads in flight for cpw = 4), even rows into one
-// accumulator and odd rows into another, and the S segment sums are added in
-// segment order in `part` (at most 2048 elements).  Every sum's order is fixed
+// accumulator and odd rows into another, and the S segment sums in `part`
+// (at most 2048 elements) are added in segment order (FP32) or as a tree
+// (FP64, where the add latency counts).  Every sum's order is fixed
 // by (rows, cols) alone: results do not depend on the block size or on whether
 // M sits in shared or global memory.
 template <typename A, typename T, typename V>
@@ -120,9 +121,16 @@ __device__ __forceinline__ void mtv(const T* __restrict__ M, int rows, int cols,
   if (S > 1) {
     __syncthreads();
     for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-      A r = part[c];
-      for (int sg = 1; sg < S; ++sg) r += part[sg * cols + c];
-      out[c] = r;
+      if constexpr (sizeof(A) == 8) {  // FP64: a three-level tree (zeros past S)
+        A r[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = k < S ? part[k * cols + c] : A(0);
+        out[c] = ((r[0] + r[1]) + (r[2] + r[3])) + ((r[4] + r[5]) + (r[6] + r[7]));
+      } else {
+        A r = part[c];
+        for (int sg = 1; sg < S; ++sg) r += part[sg * cols + c];
+        out[c] = r;
+      }
     }
   }
 }
@@ -402,18 +410,51 @@ __device__ EvalOut cta_eval(const CtaInst<T>& I, CtaWs<T>& W, const T* u, const 
   return e;
 }
 
-// Number of eigenvalues below x of the symmetric tridiagonal matrix with
-// diagonal a and off-diagonal b (b[i] joins rows i and i+1): the count of
-// negative pivots of T - x I = L D L' (Sturm sequence), in precision R.
+// Bit-level helpers of the Sturm count: sign bit, biased exponent, and an
+// exact zero, read from the representation (integer instructions: FP64
+// comparisons issue on the FP64 pipe, which runs at 1/64 of the FP32 rate on
+// this GPU).
+__device__ __forceinline__ unsigned tri_sign(double v) { return (unsigned)__double2hiint(v) >> 31; }
+__device__ __forceinline__ unsigned tri_sign(float v) { return __float_as_uint(v) >> 31; }
+__device__ __forceinline__ int tri_exp(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+__device__ __forceinline__ int tri_exp(float v) { return (int)((__float_as_uint(v) >> 23) & 0xff); }
+__device__ __forceinline__ bool tri_zero(double v) { return ((unsigned long long)__double_as_longlong(v) << 1) == 0ull; }
+__device__ __forceinline__ bool tri_zero(float v) { return (__float_as_uint(v) << 1) == 0u; }
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix T with
+// diagonal a and off-diagonal b (b[i] joins rows i and i+1), scaled so that
+// |a_i|, |b_i| <= 1: the number of sign changes along the leading principal
+// minors p_0 = 1, p_1, ..., p_m of T - x I (Sturm), from the three-term
+// recurrence p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}, in precision R.
+// No division (the pivot form d_i = p_i / p_{i-1} divides every step).  A
+// step's roundings act as relative perturbations of a few units in the last
+// place of a_i - x and b_{i-1}^2 (and a common factor of the tail of the
+// sequence, which keeps its signs), so the count is exact for a nearby
+// matrix, as for the pivot form.  With |a_i - x| <= 2 and b^2 <= 1 a minor
+// grows at most threefold per step; the pair (p_{i-1}, p_i) is rescaled by
+// 2^-+E when both fall below 2^-E or one rises above 2^E.  An exactly zero
+// minor becomes -2^-40 p_{i-1} (a tiny negative pivot).
 template <typename R>
 __device__ __forceinline__ int tri_count_below(const double* a, const double* b, int m, R x) {
+  constexpr int bias = sizeof(R) == 8 ? 1023 : 127, E = sizeof(R) == 8 ? 400 : 40;
+  const R up = sizeof(R) == 8 ? R(0x1p400) : R(0x1p40), dn = sizeof(R) == 8 ? R(0x1p-400) : R(0x1p-40);
+  R q0 = R(0), q1 = R(1);
   int cnt = 0;
-  R d = R(1);
   for (int i = 0; i < m; ++i) {
     const R bb = i > 0 ? R(b[i - 1]) : R(0);
-    d = (R(a[i]) - x) - (i > 0 ? bb * bb / d : R(0));
-    if (d == R(0)) d = R(-1e-30);
-    cnt += d < R(0);
+    R pv = (R(a[i]) - x) * q1 - (bb * bb) * q0;
+    if (tri_zero(pv)) pv = -q1 * R(0x1p-40);
+    cnt += (int)(tri_sign(pv) ^ tri_sign(q1));
+    q0 = q1;
+    q1 = pv;
+    const int e = max(tri_exp(q0), tri_exp(q1));
+    if (e < bias - E) {
+      q0 *= up;
+      q1 *= up;
+    } else if (e > bias + E) {
+      q0 *= dn;
+      q1 *= dn;
+    }
   }
   return cnt;
 }
@@ -433,14 +474,17 @@ __device__ __forceinline__ void tri_multisect(const double* a, const double* b, 
 }
 
 // Largest eigenvalue theta of the m x m symmetric tridiagonal matrix (a, b)
-// and |s_m|, the last component of its unit eigenvector, in FP64 (warp 0):
-// multisection on Sturm counts, first in FP32 to a bracket of relative width
-// 1e-6 (FP64 runs at a small fraction of the FP32 rate on this GPU), then in
-// FP64 from that bracket widened by 1e-5 (checked by two FP64 Sturm counts;
-// the Gershgorin interval when the check fails) to 1e-13; then the
-// three-term eigenvector recurrence (rescaled) in FP64 on lane 0.  Results in
-// out[0], out[1].
-__device__ inline void warp_tridiag_top(const double* a, const double* b, int m, double* out) {
+// and |s_m|, the last component of its unit eigenvector, in FP64 (one warp;
+// m <= 160).  a and b (b[0..m-2]) are first divided in place by the power of
+// two s >= the Gershgorin bound (exact), then: multisection on Sturm counts,
+// in FP32 to a bracket of relative width 1e-6, then in FP64 from that bracket
+// widened by 1e-5 (checked by two FP64 Sturm counts; the Gershgorin interval
+// when the check fails) to 1e-13; then the three-term eigenvector recurrence
+// (rescaled) at the bracket's upper end, with the reciprocals 1 / b_i
+// computed beforehand across the lanes.  Results in out[0] (theta, unscaled),
+// out[1].
+__device__ inline void warp_tridiag_top(double* a, double* b, int m, double* out) {
+  static_assert(kLzMaxSteps <= 160, "five reciprocals per lane");
   const int lane = threadIdx.x & 31;
   double glo = INFINITY, ghi = -INFINITY;
   for (int i = lane; i < m; i += 32) {
@@ -452,6 +496,34 @@ __device__ inline void warp_tridiag_top(const double* a, const double* b, int m,
     glo = fmin(glo, __shfl_xor_sync(0xffffffffu, glo, o));
     ghi = fmax(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
   }
+  const double M = fmax(fabs(glo), fabs(ghi));
+  if (!(M < INFINITY)) {  // a non-finite recurrence: no estimate
+    if (lane == 0) {
+      out[0] = M;
+      out[1] = 1.0;
+    }
+    __syncwarp();
+    return;
+  }
+  int ex = 0;
+  frexp(M, &ex);
+  const double s = M > 0.0 ? ldexp(1.0, ex) : 1.0, inv_s = 1.0 / s;
+  double rb[5];  // 1 / b_i for i = lane + 32 k
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int i = lane + 32 * k;
+    rb[k] = 0.0;
+    if (i < m) {
+      a[i] *= inv_s;
+      if (i + 1 < m) {
+        b[i] *= inv_s;
+        rb[k] = b[i] != 0.0 ? 1.0 / b[i] : 0.0;
+      }
+    }
+  }
+  __syncwarp();
+  glo *= inv_s;
+  ghi *= inv_s;
   float flo = float(glo), fhi = float(ghi);
   for (int round = 0; round < 8; ++round) {
     tri_multisect<float>(a, b, m, flo, fhi);
@@ -471,23 +543,31 @@ __device__ inline void warp_tridiag_top(const double* a, const double* b, int m,
     if (hi - lo <= 1e-13 * fmax(fabs(lo), fabs(hi))) break;
     tri_multisect<double>(a, b, m, lo, hi);
   }
-  if (lane == 0) {
-    double up = 0.0, u = 1.0, nrm2 = 1.0;
-    for (int i = 0; i + 1 < m; ++i) {
-      if (b[i] == 0.0) {  // the matrix splits: the leading block's vector ends here
-        up = 0.0; u = 1.0; nrm2 = 1.0;
-        continue;
-      }
-      const double un = ((hi - a[i]) * u - (i > 0 ? b[i - 1] * up : 0.0)) / b[i];
-      up = u;
-      u = un;
-      nrm2 += u * u;
-      if (nrm2 > 1e200) {
-        const double s = 1.0 / sqrt(nrm2);
-        up *= s; u *= s; nrm2 = 1.0;
-      }
+  // the recurrence, run by every lane alike (each holds part of the reciprocals)
+  double upv = 0.0, u = 1.0, nrm2 = 1.0;
+  for (int i = 0; i + 1 < m; ++i) {
+    const int k = i >> 5;
+    const double rk = k == 0 ? rb[0] : k == 1 ? rb[1] : k == 2 ? rb[2] : k == 3 ? rb[3] : rb[4];
+    const double rbi = __shfl_sync(0xffffffffu, rk, i & 31);
+    if (tri_zero(rbi)) {  // b_i = 0: the matrix splits, the leading block's vector ends here
+      upv = 0.0;
+      u = 1.0;
+      nrm2 = 1.0;
+      continue;
     }
-    out[0] = hi;
+    const double un = ((hi - a[i]) * u - (i > 0 ? b[i - 1] * upv : 0.0)) * rbi;
+    upv = u;
+    u = un;
+    nrm2 += u * u;
+    if (tri_exp(nrm2) > 1023 + 660) {
+      const double sq = 1.0 / sqrt(nrm2);
+      upv *= sq;
+      u *= sq;
+      nrm2 = 1.0;
+    }
+  }
+  if (lane == 0) {
+    out[0] = hi * s;
     out[1] = fabs(u) / sqrt(nrm2);
   }
   __syncwarp();
@@ -650,7 +730,8 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int which) {
       w[i] = T(rr);
       pb += rr * rr;
     }
-    const double beta = sqrt(block_sum(pb, W.red));
+    const double bsq = block_sum(pb, W.red);
+    const double beta = sqrt(bsq), rbeta = rsqrt(bsq);  // two short chains side by side, no division
     if (threadIdx.x == 0) {
       al[j] = alpha;
       be[j] = beta;
@@ -667,13 +748,155 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int which) {
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       vp[i] = v[i];
-      v[i] = T(double(w[i]) / beta);
+      v[i] = T(double(w[i]) * rbeta);
     }
     beta_prev = beta;
     __syncthreads();
   }
   __syncthreads();
   return lz_estimate(theta, r, exhausted, sizeof(T) == 8 ? 1.2e-16 : 6.0e-8);
+}
+
+// Both Lanczos runs of an FP64 instance (Q and G'G) in one loop: each step
+// makes the three products (Q v1 beside G v2, then G' (G v2)) and takes the two
+// runs' dot products in shared block reductions, so the runs share every
+// barrier and keep two independent product chains on the FP64 pipe (at
+// n = 50 the two runs one after the other were 1.0 of the 1.4 ms of a solve,
+// the FP64 pipe about a quarter busy and the warps mostly waiting at
+// barriers), and the two tridiagonal eigenproblems run at once on two warps.
+// Each run's arithmetic is the single run's (cta_lanczos): the same start
+// vector, step count, products and estimate.  Extra buffers: the B chain's
+// Q x slots hold the second run's alpha and beta (n doubles each).
+// Two block sums at once where only threads below `act` hold nonzero values
+// (vectors of length act < blockDim): the other warps skip the shuffles,
+// which would only keep the SM's FP64 pipe busy with zeros, and warp 0 adds
+// the warp sums as a butterfly tree.
+__device__ __forceinline__ void block_sum2(double a, double b, int act, double* red, double* out) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nwa = (min(act, (int)blockDim.x) + 31) >> 5;
+  if (w < nwa) {
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xffffffffu, a, o);
+      b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+  }
+  __syncthreads();
+  if (w < nwa && l == 0) {
+    red[w] = a;
+    red[16 + w] = b;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double sa = l < nwa ? red[l] : 0.0, sb = l < nwa ? red[16 + l] : 0.0;
+    for (int o = 1; o < nwa; o <<= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if (l == 0) {
+      red[32] = sa;
+      red[33] = sb;
+    }
+  }
+  __syncthreads();
+  out[0] = red[32];
+  out[1] = red[33];
+}
+
+__device__ inline void cta_lanczos_pair(const CtaInst<double>& I, CtaWs<double>& W, double* lmax_Q, double* normG2) {
+  const int n = I.n, p = I.p;
+  double *v1 = W.A.x, *vp1 = W.B.x, *w1 = W.A.Qx;            // Q run
+  double *v2 = W.A.xp, *vp2 = W.A.xn, *w2 = W.A.Qxp, *t = W.A.Gx;  // G'G run
+  double *al1 = W.dn, *be1 = W.usum, *al2 = W.B.Qx, *be2 = W.B.Qxp;
+  double ps = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double s = lz_start((unsigned long long)i);
+    ps += s * s;
+  }
+  const double inv = 1.0 / sqrt(block_sum(ps, W.red));
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    v1[i] = v2[i] = lz_start((unsigned long long)i) * inv;
+    vp1[i] = vp2[i] = 0.0;
+  }
+  __syncthreads();
+  const int ksteps = min(lz_min_steps(n), kLzMaxSteps);
+  double bprev1 = 0.0, bprev2 = 0.0, beta1 = 0.0, beta2 = 0.0;
+  int m1 = 0, m2 = 0;  // steps recorded by each run (a run stops at an invariant subspace)
+  bool on1 = true, on2 = true;
+  for (int j = 0; j < ksteps && (on1 || on2); ++j) {
+    // Q v1 and G v2 read different vectors and write different outputs: no
+    // barrier between them, each with its own half of `part` (an FP64 split
+    // product holds at most 256 partial sums, see mtv)
+    if (on1) mtv<double>(W.Q, n, n, n, v1, w1, W.part);
+    if (on2) mtv<double>(W.GT, n, p, p, v2, t, W.part + 1024);
+    __syncthreads();
+    if (on2) mtv<double>(W.G, p, n, n, t, w2, W.part);
+    __syncthreads();
+    double pa1 = 0.0, pa2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (on1) pa1 += v1[i] * w1[i];
+      if (on2) pa2 += v2[i] * w2[i];
+    }
+    double al[2];
+    block_sum2(pa1, pa2, n, W.red, al);
+    double pb1 = 0.0, pb2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (on1) {
+        const double rr = w1[i] - al[0] * v1[i] - bprev1 * vp1[i];
+        w1[i] = rr;
+        pb1 += rr * rr;
+      }
+      if (on2) {
+        const double rr = w2[i] - al[1] * v2[i] - bprev2 * vp2[i];
+        w2[i] = rr;
+        pb2 += rr * rr;
+      }
+    }
+    double bb[2];
+    block_sum2(pb1, pb2, n, W.red, bb);
+    const bool last = j + 1 == ksteps;
+    const double rb1 = rsqrt(bb[0]), rb2 = rsqrt(bb[1]);
+    if (on1) {
+      beta1 = sqrt(bb[0]);
+      if (threadIdx.x == 0) {
+        al1[j] = al[0];
+        be1[j] = beta1;
+      }
+      m1 = j + 1;
+    }
+    if (on2) {
+      beta2 = sqrt(bb[1]);
+      if (threadIdx.x == 0) {
+        al2[j] = al[1];
+        be2[j] = beta2;
+      }
+      m2 = j + 1;
+    }
+    const bool go1 = on1 && !last && beta1 > 1e-300, go2 = on2 && !last && beta2 > 1e-300;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      if (go1) {
+        vp1[i] = v1[i];
+        v1[i] = w1[i] * rb1;
+      }
+      if (go2) {
+        vp2[i] = v2[i];
+        v2[i] = w2[i] * rb2;
+      }
+    }
+    if (go1) bprev1 = beta1;
+    if (go2) bprev2 = beta2;
+    on1 = go1;
+    on2 = go2;
+    __syncthreads();
+  }
+  // the two tridiagonal problems at once, on warps 0 and 1 (two schedulers)
+  __syncthreads();
+  if (threadIdx.x < 32) warp_tridiag_top(al1, be1, m1, W.red + 34);
+  else if (threadIdx.x < 64) warp_tridiag_top(al2, be2, m2, W.red + 36);
+  __syncthreads();
+  const double ex = 1.2e-16;
+  *lmax_Q = lz_estimate(W.red[34], beta1 * W.red[35], !(beta1 > 1e-300) || m1 == n, ex);
+  *normG2 = lz_estimate(W.red[36], beta2 * W.red[37], !(beta2 > 1e-300) || m2 == n, ex);
+  __syncthreads();
 }
 
 // Guaranteed upper bounds (no estimate): lambda_max(Q) <= min(max_i sum_j |Q_ij|
@@ -781,6 +1004,9 @@ __device__ void cta_solve(CtaInst<T>& I, unsigned char* smem, size_t smem_bytes)
   }
   __syncthreads();
   // FP64 constants (a1): lambda_max(Q), ||G||^2, then L_L, sigma_L, L_d, rho
+  if constexpr (sizeof(T) == 8) {  // both estimates wanted: the two Lanczos runs in one loop
+    if (isnan(I.lmax_Q) && isnan(I.normG2) && p > 0 && !I.lip_bound) cta_lanczos_pair(I, W, &I.lmax_Q, &I.normG2);
+  }
   if (isnan(I.lmax_Q)) I.lmax_Q = I.lip_bound ? cta_bound<T>(I, W, 0) : cta_lanczos<T>(I, W, 0);
   if (isnan(I.normG2)) I.normG2 = p > 0 ? (I.lip_bound ? cta_bound<T>(I, W, 1) : cta_lanczos<T>(I, W, 1)) : 0.0;
   const double lmin = isnan(I.lmin_Q) ? 0.0 : I.lmin_Q;

@@ -41,20 +41,22 @@ __device__ __forceinline__ T clampT(T v, T lo, T hi) {
 }
 
 // Deterministic block-wide sum of one double per thread.  Lane 0 of warp w
-// stores the warp's shuffle-tree sum; thread 0 adds the warps in order.  The
-// result depends only on the values and blockDim, never on scheduling.
-// `red` must hold 33 doubles of shared memory.
+// stores the warp's shuffle-tree sum; warp 0 adds the warp sums as a
+// butterfly tree (three dependent FP64 adds for eight warps instead of eight:
+// FP64 latency sets the cost of these sums).  The result depends only on the
+// values and blockDim, never on scheduling.  `red` must hold 33 doubles of
+// shared memory.
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
+  if (w == 0) {
     const int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i) s += red[i];
-    red[32] = s;
+    double s = l < nw ? red[l] : 0.0;
+    for (int o = 1; o < nw; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (l == 0) red[32] = s;
   }
   __syncthreads();
   return red[32];

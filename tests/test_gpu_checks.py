@@ -62,6 +62,32 @@ def test_lanczos_finds_a_top_eigenvector_orthogonal_to_ones(ctx, engine_name, n,
     assert inf <= eps * 1.01 and gap <= eps * 1.01, (inf, gap)
 
 
+@pytest.mark.parametrize("n,p", [(50, 50), (61, 17), (300, 120)])
+def test_paired_fp64_lanczos_equals_the_single_runs(ctx, n, p):
+    """With both constants wanted, an FP64 thread-block solve runs the Q and G'G Lanczos
+    iterations in one loop; each must return exactly what its run alone returns (the run alone
+    is taken when the other constant is supplied)."""
+    from paper_1504_05708_gb300 import duquad as D
+    inst = W.single_dense(n=n, p=p, seed=300 + n, lam_lo=1.0, lam_hi=100.0)
+    o = D.opts("DFGM", fixed_outer=1, fixed_inner=1, engine=D.ENGINE_CTA)
+    P = gpu_problem(ctx, inst, D.FP64)
+    P.solve(o)
+    lmax, _, nG2 = P.constants()
+    P.close()
+    Pq = gpu_problem(ctx, inst, D.FP64, normG2=nG2)
+    Pq.solve(o)
+    lmax_alone = Pq.constants()[0]
+    Pq.close()
+    Pg = gpu_problem(ctx, inst, D.FP64, lmax_Q=lmax)
+    Pg.solve(o)
+    nG2_alone = Pg.constants()[2]
+    Pg.close()
+    assert lmax == lmax_alone and nG2 == nG2_alone, (lmax, lmax_alone, nG2, nG2_alone)
+    # upper bounds (the top of these spectra is clustered: theta + 2 r can sit several % above)
+    assert lmax >= np.linalg.eigvalsh(inst.Q)[-1] * (1 - 1e-12)
+    assert nG2 >= np.linalg.norm(inst.G, 2) ** 2 * (1 - 1e-12)
+
+
 @pytest.mark.parametrize("engine_name,n,p", [("CTA", 120, 50), ("GRID", 400, 150)])
 def test_guaranteed_bound_mode(ctx, engine_name, n, p):
     """DQ_LIP_BOUND: min(Gershgorin, Frobenius) and min(||G||_1 ||G||_inf, ||G||_F^2) are at
