@@ -60,7 +60,8 @@ struct CtaInst {
 // dependent chain per lane left most warps waiting at the next barrier, e.g.
 // 64 lanes with 25 FMAs each at n = 50).  A unit walks its rows
 // four at a time (16 loads in flight for cpw = 4), even rows into one
-// accumulator and odd rows into another, and the S segment sums in `part`
+// accumulator and odd rows into another (four accumulators by row mod 4
+// measured slower for FP64 at n = 50), and the S segment sums in `part`
 // (at most 2048 elements) are added in segment order (FP32) or as a tree
 // (FP64, where the add latency counts).  Every sum's order is fixed
 // by (rows, cols) alone: results do not depend on the block size or on whether
@@ -216,7 +217,7 @@ template <typename T>
 __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* mu) {
   const int n = I.n, p = I.p;
   const bool aug = I.rho > 0.0;
-  const T rho = T(I.rho), L = T(I.LL);
+  const T rho = T(I.rho), invL = T(1.0 / I.LL);
   if (!aug) {  // c = q + G' mu, fixed over the inner loop
     if (p > 0) {
       mtv<T>(W.G, p, n, n, mu, W.c, W.part);
@@ -230,6 +231,13 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
   __syncthreads();
   const bool fgm_sigma = I.sigma > 0.0;
   const double beta_sigma = (sqrt(I.LL) - sqrt(I.sigma)) / (sqrt(I.LL) + sqrt(I.sigma));
+  // theta: thread 0's copy of the FGM sequence.  The next weight beta_{k+1}
+  // depends on theta_k alone, so thread 0 forms it during iteration k and
+  // publishes it through W.red[38 + ((k + 1) & 1)] (double-buffered: the slot
+  // it writes in iteration k + 1 was read before the barrier that follows
+  // iteration k's step); every other thread skips the FP64 sqrt and
+  // division, which a block of 8 to 16 warps would otherwise repeat on the
+  // slow FP64 pipe each iteration.
   double theta = 1.0, beta = 0.0;
   const int m = I.inner_check_every > 0 ? I.inner_check_every : 1;
   int k = 0;
@@ -252,7 +260,7 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
         const T y = S.x[i] + b * (S.x[i] - S.xp[i]);
         const T Qy = S.Qx[i] + b * (S.Qx[i] - S.Qxp[i]);
         const T gr = aug ? Qy + I.q[i] + W.tn[i] : Qy + W.c[i];
-        S.xn[i] = clampT(y - gr / L, I.lb[i], I.ub[i]);
+        S.xn[i] = clampT(y - gr * invL, I.lb[i], I.ub[i]);
       }
     };
     if constexpr (sizeof(T) == 8) {
@@ -267,7 +275,7 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
           const T y = S.x[i] + b * (S.x[i] - S.xp[i]);
           const T Qy = S.Qx[i] + b * (S.Qx[i] - S.Qxp[i]);
           const T gr = aug ? Qy + I.q[i] + W.tn[i] : Qy + W.c[i];
-          const T st = gr / L, s = y - st;
+          const T st = gr * invL, s = y - st;
           const T xn = clampT(s, I.lb[i], I.ub[i]);
           S.xn[i] = xn;
           // y - x^k is the step itself where the box is inactive (no cancellation)
@@ -281,6 +289,11 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
     } else {
       plain_step();
     }
+    if (!fgm_sigma && threadIdx.x == 0) {  // step 2 weight of the next iteration (Sec. 2.1)
+      const double tn1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
+      W.red[38 + ((k + 1) & 1)] = (theta - 1.0) / tn1;
+      theta = tn1;
+    }
     __syncthreads();
     mtv<T>(W.Q, n, n, n, S.xn, S.Qxn, W.part);
     if (aug) {
@@ -289,13 +302,7 @@ __device__ int cta_fom(const CtaInst<T>& I, CtaWs<T>& W, XState<T>& S, const T* 
     }
     __syncthreads();
     // step 2 weight beta_k (GM/FGM/FGM_sigma rules, Sec. 2.1)
-    if (fgm_sigma) {
-      beta = beta_sigma;
-    } else {
-      const double tn1 = 0.5 * (1.0 + sqrt(1.0 + 4.0 * theta * theta));
-      beta = (theta - 1.0) / tn1;
-      theta = tn1;
-    }
+    beta = fgm_sigma ? beta_sigma : W.red[38 + ((k + 1) & 1)];
     T* t;
     t = S.xp; S.xp = S.x; S.x = S.xn; S.xn = t;
     t = S.Qxp; S.Qxp = S.Qx; S.Qx = S.Qxn; S.Qxn = t;
