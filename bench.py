@@ -999,7 +999,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="large", choices=["large", "eq", "small", "uneven", "mpc", "served",
                                                              "sweep", "sparse"])
-    ap.add_argument("--out", default="gpurun_out/sweep.json", help="sweep workload: where the table goes")
+    ap.add_argument("--out", default="sweep_table.json", help="sweep workload: where the table goes")
     ap.add_argument("--count", type=int, default=None)
     ap.add_argument("--rate", type=float, default=20000.0)
     ap.add_argument("--duration", type=float, default=0.5)
