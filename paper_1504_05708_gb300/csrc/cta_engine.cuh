@@ -738,7 +738,12 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int which) {
       pb += rr * rr;
     }
     const double bsq = block_sum(pb, W.red);
-    const double beta = sqrt(bsq), rbeta = rsqrt(bsq);  // two short chains side by side, no division
+    // beta and 1/beta (no division): one chain each on lane 0 of two warps,
+    // published through W.red[34..35], instead of every warp repeating both
+    for (int t = threadIdx.x >> 5; t < 2; t += (blockDim.x + 31) >> 5)
+      if ((threadIdx.x & 31) == 0) W.red[34 + t] = t ? rsqrt(bsq) : sqrt(bsq);
+    __syncthreads();
+    const double beta = W.red[34], rbeta = W.red[35];
     if (threadIdx.x == 0) {
       al[j] = alpha;
       be[j] = beta;
@@ -860,10 +865,16 @@ __device__ inline void cta_lanczos_pair(const CtaInst<double>& I, CtaWs<double>&
     }
     double bb[2];
     block_sum2(pb1, pb2, n, W.red, bb);
+    // beta and 1/beta of both runs: one chain each on lane 0 of four warps
+    // (four schedulers), published through W.red[34..37], instead of every
+    // warp repeating all four on the shared FP64 pipe
+    for (int t = threadIdx.x >> 5; t < 4; t += (blockDim.x + 31) >> 5)
+      if ((threadIdx.x & 31) == 0) W.red[34 + t] = (t & 1) ? rsqrt(bb[t >> 1]) : sqrt(bb[t >> 1]);
+    __syncthreads();
     const bool last = j + 1 == ksteps;
-    const double rb1 = rsqrt(bb[0]), rb2 = rsqrt(bb[1]);
+    const double rb1 = W.red[35], rb2 = W.red[37];
     if (on1) {
-      beta1 = sqrt(bb[0]);
+      beta1 = W.red[34];
       if (threadIdx.x == 0) {
         al1[j] = al[0];
         be1[j] = beta1;
@@ -871,7 +882,7 @@ __device__ inline void cta_lanczos_pair(const CtaInst<double>& I, CtaWs<double>&
       m1 = j + 1;
     }
     if (on2) {
-      beta2 = sqrt(bb[1]);
+      beta2 = W.red[36];
       if (threadIdx.x == 0) {
         al2[j] = al[1];
         be2[j] = beta2;
