@@ -429,8 +429,10 @@ __device__ __forceinline__ bool tri_zero(double v) { return ((unsigned long long
 __device__ __forceinline__ bool tri_zero(float v) { return (__float_as_uint(v) << 1) == 0u; }
 
 // Number of eigenvalues below x of the symmetric tridiagonal matrix T with
-// diagonal a and off-diagonal b (b[i] joins rows i and i+1), scaled so that
-// |a_i|, |b_i| <= 1: the number of sign changes along the leading principal
+// diagonal a and squared off-diagonal bq (bq[i] = b_i^2, b_i joining rows i
+// and i + 1), in precision R and scaled so that |a_i|, |b_i| <= 1 (the FP32
+// rounds read float copies: no conversion from FP64 per step): the number of
+// sign changes along the leading principal
 // minors p_0 = 1, p_1, ..., p_m of T - x I (Sturm), from the three-term
 // recurrence p_i = (a_i - x) p_{i-1} - b_{i-1}^2 p_{i-2}, in precision R.
 // No division (the pivot form d_i = p_i / p_{i-1} divides every step).  A
@@ -442,14 +444,14 @@ __device__ __forceinline__ bool tri_zero(float v) { return (__float_as_uint(v) <
 // 2^-+E when both fall below 2^-E or one rises above 2^E.  An exactly zero
 // minor becomes -2^-40 p_{i-1} (a tiny negative pivot).
 template <typename R>
-__device__ __forceinline__ int tri_count_below(const double* a, const double* b, int m, R x) {
+__device__ __forceinline__ int tri_count_below(const R* a, const R* bq, int m, R x) {
   constexpr int bias = sizeof(R) == 8 ? 1023 : 127, E = sizeof(R) == 8 ? 400 : 40;
   const R up = sizeof(R) == 8 ? R(0x1p400) : R(0x1p40), dn = sizeof(R) == 8 ? R(0x1p-400) : R(0x1p-40);
   R q0 = R(0), q1 = R(1);
   int cnt = 0;
   for (int i = 0; i < m; ++i) {
-    const R bb = i > 0 ? R(b[i - 1]) : R(0);
-    R pv = (R(a[i]) - x) * q1 - (bb * bb) * q0;
+    const R b2 = i > 0 ? bq[i - 1] : R(0);
+    R pv = (a[i] - x) * q1 - b2 * q0;
     if (tri_zero(pv)) pv = -q1 * R(0x1p-40);
     cnt += (int)(tri_sign(pv) ^ tri_sign(q1));
     q0 = q1;
@@ -469,10 +471,10 @@ __device__ __forceinline__ int tri_count_below(const double* a, const double* b,
 // One round of 33-way multisection of [lo, hi] (which holds the largest
 // eigenvalue) by the 32 lanes of a warp: lane l tests lo + (hi - lo)(l + 1)/33.
 template <typename R>
-__device__ __forceinline__ void tri_multisect(const double* a, const double* b, int m, R& lo, R& hi) {
+__device__ __forceinline__ void tri_multisect(const R* a, const R* bq, int m, R& lo, R& hi) {
   const int lane = threadIdx.x & 31;
   const R x = lo + (hi - lo) * (R(lane + 1) / R(33));
-  const unsigned ball = __ballot_sync(0xffffffffu, tri_count_below<R>(a, b, m, x) == m);  // x above all
+  const unsigned ball = __ballot_sync(0xffffffffu, tri_count_below<R>(a, bq, m, x) == m);  // x above all
   const int first = ball ? __ffs(ball) - 1 : 32;
   const R nhi = first < 32 ? __shfl_sync(0xffffffffu, x, first) : hi;
   const R nlo = first > 0 ? __shfl_sync(0xffffffffu, x, first > 0 ? first - 1 : 0) : lo;
@@ -482,15 +484,16 @@ __device__ __forceinline__ void tri_multisect(const double* a, const double* b, 
 
 // Largest eigenvalue theta of the m x m symmetric tridiagonal matrix (a, b)
 // and |s_m|, the last component of its unit eigenvector, in FP64 (one warp;
-// m <= 160).  a and b (b[0..m-2]) are first divided in place by the power of
-// two s >= the Gershgorin bound (exact), then: multisection on Sturm counts,
+// m <= 160).  a is first divided in place by the power of two s >= the
+// Gershgorin bound (exact) and b (b[0..m-2]) replaced by (b_i / s)^2, with
+// float copies in fa, fb (m floats each, caller's scratch) and the
+// reciprocals s / b_i across the lanes; then: multisection on Sturm counts,
 // in FP32 to a bracket of relative width 1e-6, then in FP64 from that bracket
 // widened by 1e-5 (checked by two FP64 Sturm counts; the Gershgorin interval
 // when the check fails) to 1e-13; then the three-term eigenvector recurrence
-// (rescaled) at the bracket's upper end, with the reciprocals 1 / b_i
-// computed beforehand across the lanes.  Results in out[0] (theta, unscaled),
-// out[1].
-__device__ inline void warp_tridiag_top(double* a, double* b, int m, double* out) {
+// (rescaled) at the bracket's upper end, taking b_{i-1} as
+// b_{i-1}^2 (1 / b_{i-1}).  Results in out[0] (theta, unscaled), out[1].
+__device__ inline void warp_tridiag_top(double* a, double* b, int m, double* out, float* fa, float* fb) {
   static_assert(kLzMaxSteps <= 160, "five reciprocals per lane");
   const int lane = threadIdx.x & 31;
   double glo = INFINITY, ghi = -INFINITY;
@@ -521,10 +524,14 @@ __device__ inline void warp_tridiag_top(double* a, double* b, int m, double* out
     const int i = lane + 32 * k;
     rb[k] = 0.0;
     if (i < m) {
-      a[i] *= inv_s;
+      const double as = a[i] * inv_s;
+      a[i] = as;
+      fa[i] = float(as);
       if (i + 1 < m) {
-        b[i] *= inv_s;
-        rb[k] = b[i] != 0.0 ? 1.0 / b[i] : 0.0;
+        const double bs = b[i] * inv_s, b2 = bs * bs;
+        rb[k] = bs != 0.0 ? 1.0 / bs : 0.0;
+        b[i] = b2;
+        fb[i] = float(b2);
       }
     }
   }
@@ -533,7 +540,7 @@ __device__ inline void warp_tridiag_top(double* a, double* b, int m, double* out
   ghi *= inv_s;
   float flo = float(glo), fhi = float(ghi);
   for (int round = 0; round < 8; ++round) {
-    tri_multisect<float>(a, b, m, flo, fhi);
+    tri_multisect<float>(fa, fb, m, flo, fhi);
     if (fhi - flo <= 1e-6f * fmaxf(fabsf(flo), fabsf(fhi))) break;
   }
   const double sc = fmax(fabs(double(flo)), fabs(double(fhi)));
@@ -551,18 +558,20 @@ __device__ inline void warp_tridiag_top(double* a, double* b, int m, double* out
     tri_multisect<double>(a, b, m, lo, hi);
   }
   // the recurrence, run by every lane alike (each holds part of the reciprocals)
-  double upv = 0.0, u = 1.0, nrm2 = 1.0;
+  double upv = 0.0, u = 1.0, nrm2 = 1.0, rbp = 0.0;
   for (int i = 0; i + 1 < m; ++i) {
     const int k = i >> 5;
     const double rk = k == 0 ? rb[0] : k == 1 ? rb[1] : k == 2 ? rb[2] : k == 3 ? rb[3] : rb[4];
     const double rbi = __shfl_sync(0xffffffffu, rk, i & 31);
+    const double bprev = i > 0 ? b[i - 1] * rbp : 0.0;  // b_{i-1} = b_{i-1}^2 / b_{i-1}
+    rbp = rbi;
     if (tri_zero(rbi)) {  // b_i = 0: the matrix splits, the leading block's vector ends here
       upv = 0.0;
       u = 1.0;
       nrm2 = 1.0;
       continue;
     }
-    const double un = ((hi - a[i]) * u - (i > 0 ? b[i - 1] * upv : 0.0)) * rbi;
+    const double un = ((hi - a[i]) * u - bprev * upv) * rbi;
     upv = u;
     u = un;
     nrm2 += u * u;
@@ -665,7 +674,7 @@ __device__ inline void warp_lanczos(const CtaInst<float>& I, CtaWs<float>& W, in
     const bool invariant = !(beta > 1e-300);
     if (invariant || j + 1 == ksteps) {
       __syncwarp();
-      warp_tridiag_top(al, be, j + 1, W.red + 34);
+      warp_tridiag_top(al, be, j + 1, W.red + 34, (float*)W.A.xp, (float*)W.A.xn);
       __syncwarp();
       theta = W.red[34];
       r = beta * W.red[35];
@@ -751,7 +760,7 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int which) {
     const bool invariant = !(beta > 1e-300);
     if (invariant || j + 1 == ksteps) {
       __syncthreads();
-      if (threadIdx.x < 32) warp_tridiag_top(al, be, j + 1, W.red + 34);
+      if (threadIdx.x < 32) warp_tridiag_top(al, be, j + 1, W.red + 34, (float*)W.A.xp, (float*)W.A.xn);
       __syncthreads();
       theta = W.red[34];
       r = beta * W.red[35];
@@ -908,8 +917,9 @@ __device__ inline void cta_lanczos_pair(const CtaInst<double>& I, CtaWs<double>&
   }
   // the two tridiagonal problems at once, on warps 0 and 1 (two schedulers)
   __syncthreads();
-  if (threadIdx.x < 32) warp_tridiag_top(al1, be1, m1, W.red + 34);
-  else if (threadIdx.x < 64) warp_tridiag_top(al2, be2, m2, W.red + 36);
+  // float scratch: a free n-double buffer per run holds both copies (2m <= 2n floats)
+  if (threadIdx.x < 32) warp_tridiag_top(al1, be1, m1, W.red + 34, (float*)W.A.Qxn, (float*)W.A.Qxn + m1);
+  else if (threadIdx.x < 64) warp_tridiag_top(al2, be2, m2, W.red + 36, (float*)W.B.Qxn, (float*)W.B.Qxn + m2);
   __syncthreads();
   const double ex = 1.2e-16;
   *lmax_Q = lz_estimate(W.red[34], beta1 * W.red[35], !(beta1 > 1e-300) || m1 == n, ex);
