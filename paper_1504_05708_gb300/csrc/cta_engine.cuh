@@ -596,7 +596,8 @@ __device__ inline void warp_tridiag_top(double* a, double* b, int m, double* out
 // T_k and its residual r = beta_k |s_k| give lz_estimate (theta / (1 - eps)
 // or theta + 2 r, whichever is larger).  Products in T, the three-term
 // recurrence and the tridiagonal eigenproblem in FP64.
-// Scratch: A.x, B.x, A.Qx, A.Gx, dn, usum.
+// Scratch: A.x, B.x, A.Qx, A.Gx, dn, usum (and A.xp, A.xn for the
+// tridiagonal solve's float copies).
 // The same Lanczos for FP32 instances with n, p <= 64, run by warp 0 alone
 // (the block waits once): at these sizes the block version spent most of
 // its time in the barriers of its block reductions (about nine per step).
@@ -787,7 +788,8 @@ __device__ double cta_lanczos(const CtaInst<T>& I, CtaWs<T>& W, int which) {
 // barriers), and the two tridiagonal eigenproblems run at once on two warps.
 // Each run's arithmetic is the single run's (cta_lanczos): the same start
 // vector, step count, products and estimate.  Extra buffers: the B chain's
-// Q x slots hold the second run's alpha and beta (n doubles each).
+// Q x slots hold the second run's alpha and beta (n doubles each), and A.Qxn
+// and B.Qxn the float copies of the two tridiagonal solves.
 // Two block sums at once where only threads below `act` hold nonzero values
 // (vectors of length act < blockDim): the other warps skip the shuffles,
 // which would only keep the SM's FP64 pipe busy with zeros, and warp 0 adds
